@@ -1,0 +1,483 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every check here is independent of the oracle's own formulas: closed forms,
+invariants, brute force and independent library quadrature.  A plausible
+slip anywhere in the oracle (dropped term, wrong sign or index, transposed
+operand) should fail one of them.  (arXiv 2311.01492: Sec. 2.1, 2.2, 3.1,
+3.3, 4.1.1, App. A.)
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2311_01492_gb300 import synth as S
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CELL32 = 10.0 * S.MPC_CM / 32  # 0.3125 Mpc
+
+
+def dtau_of(cell, nH, xHI):
+    return O.SIGMA0 * cell * nH * xHI
+
+
+# ------------------------------------------------------------ shells (Sec. 3.3)
+@pytest.mark.parametrize("q", list(range(0, 21)))
+def test_shell_is_octahedral_surface(q):
+    got = O.shell_list(q)
+    brute = {(a, b, c) for a in range(-q, q + 1) for b in range(-q, q + 1)
+             for c in range(-q, q + 1) if abs(a) + abs(b) + abs(c) == q}
+    assert len(got) == len(brute)
+    assert {tuple(x) for x in got} == brute
+    # |S_q| = 4 q^2 + 2 (Sec. 3.3) and the top part k >= k_s holds 2q(q+1)+1 (App. A)
+    assert len(got) == (1 if q == 0 else 4 * q * q + 2)
+    if q > 0:
+        assert int(np.sum(got[:, 2] >= 0)) == 2 * q * (q + 1) + 1
+
+
+def _neighbours(d):
+    """Entry-plane interpolants of Eq. raga, re-derived here from the text."""
+    ad = [abs(x) for x in d]
+    m = max(ad)
+    ax = 2 if ad[2] == m else (1 if ad[1] == m else 0)
+    others = [a for a in range(3) if a != ax]
+    sg = [int(np.sign(x)) for x in d]
+    e1 = list(d)
+    e1[ax] -= sg[ax]
+    e2 = list(e1)
+    e2[others[0]] -= sg[others[0]]
+    e3 = list(e1)
+    e3[others[1]] -= sg[others[1]]
+    e4 = list(e2)
+    e4[others[1]] -= sg[others[1]]
+    return [e1, e2, e3, e4]
+
+
+def test_interpolants_are_causal_and_inside_the_ball():
+    """Every interpolant of a cell in S_q lies in S_{q-1}, S_{q-2} or S_{q-3}
+    (Sec. 3.3 causality) and is no farther from the source."""
+    L = 10
+    for d in itertools.product(range(-L, L + 1), repeat=3):
+        q = sum(abs(x) for x in d)
+        if q == 0:
+            continue
+        r2 = sum(x * x for x in d)
+        for e in _neighbours(d):
+            qe = sum(abs(x) for x in e)
+            assert q - 3 <= qe <= q - 1
+            assert sum(x * x for x in e) < r2
+
+
+@pytest.mark.parametrize("n,R,src", [(16, 9.5, (8, 8, 8)), (15, 7.0, (0, 14, 3)),
+                                     (12, 20.0, (11, 0, 5)), (17, 30.0, (3, 3, 16))])
+def test_oracle_reads_only_computed_cells(n, R, src):
+    """NaN-filled scratch: the shell order never reads a cell before it is computed."""
+    nH = S.lognormal_field(n, 1e-3, seed=7)
+    xHI = S.uniform_xhi(n, seed=8)
+    tab = O.make_table("grey_exact")
+    r = O.raytrace(n, CELL32, nH, xHI, [src], [1e50], [R], tab, coldens_src=0, debug=True)
+    assert np.all(np.isfinite(r["gamma"]))
+
+
+# ----------------------------------------- column density closed forms (Sec. 3.1)
+def _uniform(n=32, R=15.0, xhi=1.0, nH=1e-3, tab=None, ndot=1e54):
+    c = n // 2
+    tab = tab or O.make_table("grey_exact")
+    r = O.raytrace(n, CELL32, np.full(n ** 3, nH), np.full(n ** 3, xhi), [[c, c, c]],
+                   [ndot], [R], tab, coldens_src=0, debug=True)
+    tau = (r["coldens"] * O.SIGMA0).reshape(n, n, n)
+    return r, tau, c, dtau_of(CELL32, nH, xhi)
+
+
+def test_axis_and_diagonal_column_density_exact():
+    r, tau, c, dt = _uniform()
+    for k in range(1, 16):
+        for (a, b, cc) in [(0, 0, 1), (0, 0, -1), (0, 1, 0), (0, -1, 0), (1, 0, 0), (-1, 0, 0)]:
+            assert tau[c + a * k, c + b * k, c + cc * k] == pytest.approx(dt * (k + 0.5), rel=1e-13)
+    for k in range(1, 11):  # planar diagonals, |Delta| = sqrt(2) k <= 15
+        for sa, sb in itertools.product((1, -1), repeat=2):
+            want = math.sqrt(2.0) * dt * (k + 0.5)
+            assert tau[c + sa * k, c + sb * k, c] == pytest.approx(want, rel=1e-13)
+            assert tau[c + sa * k, c, c + sb * k] == pytest.approx(want, rel=1e-13)
+            assert tau[c, c + sa * k, c + sb * k] == pytest.approx(want, rel=1e-13)
+    for k in range(1, 9):  # body diagonals
+        for s3 in itertools.product((1, -1), repeat=3):
+            want = math.sqrt(3.0) * dt * (k + 0.5)
+            assert tau[c + s3[0] * k, c + s3[1] * k, c + s3[2] * k] == pytest.approx(want, rel=1e-13)
+    assert tau[c, c, c] == pytest.approx(0.5 * dt, rel=1e-15)
+
+
+def test_even_window_clips_positive_side():
+    """Even N: offsets in [-N/2, N/2-1] (App. A): +16 is not traced on a 32^3 grid."""
+    r, tau, c, dt = _uniform(R=16.0)
+    assert tau[c, c, c - 16] == pytest.approx(dt * 16.5, rel=1e-13)
+    assert tau[c, c, (c + 16) % 32] == pytest.approx(dt * 16.5, rel=1e-13)  # same cell, traced from -16
+    assert tau[c, c, c + 15] == pytest.approx(dt * 15.5, rel=1e-13)
+
+
+def test_sc_matches_long_characteristics():
+    """Long characteristics (exact ray integration) agree exactly on axes and
+    diagonals (Sec. 3.1, last paragraph) and approximately elsewhere."""
+    n, R = 16, 7.0
+    c = 8
+    nH = np.full(n ** 3, 1e-3)
+    xHI = np.full(n ** 3, 1.0)
+    sc = O.raytrace(n, CELL32, nH, xHI, [[c, c, c]], [1e54], [R], O.make_table("grey_exact"),
+                    coldens_src=0)["coldens"] * O.SIGMA0
+    lc = O.lc_tau(n, CELL32, nH, xHI, (c, c, c), R)
+    sc3, lc3 = sc.reshape(n, n, n), lc.reshape(n, n, n)
+    dmax = []
+    for d in itertools.product(range(-7, 8), repeat=3):
+        r2 = d[0] ** 2 + d[1] ** 2 + d[2] ** 2
+        if r2 > 49:
+            continue
+        p = (c + d[0], c + d[1], c + d[2])
+        a = sorted(abs(x) for x in d)
+        special = (a[0] == a[1] == 0) or (a[0] == 0 and a[1] == a[2]) or (a[0] == a[1] == a[2])
+        rel = abs(sc3[p] - lc3[p]) / lc3[p]
+        if special:
+            assert rel < 1e-13, d
+        else:
+            dmax.append(rel)
+            # interpolating path lengths is a small-angle approximation: worst
+            # next to the source, improving outwards
+            assert rel < (0.09 if r2 < 16 else 0.06), d
+    assert np.median(dmax) < 0.05
+    # A clumpy medium: SC stays an approximation of LC (fuzzy shadows, Sec. 4.1.4).
+    nH2 = S.lognormal_field(n, 1e-3, sigma_ln=0.5, seed=3).reshape(-1)
+    sc2 = O.raytrace(n, CELL32, nH2, xHI, [[c, c, c]], [1e54], [R], O.make_table("grey_exact"),
+                     coldens_src=0)["coldens"] * O.SIGMA0
+    lc2 = O.lc_tau(n, CELL32, nH2, xHI, (c, c, c), R)
+    m = np.isfinite(lc2) & (lc2 > 0)
+    rel2 = np.abs(sc2[m] - lc2[m]) / lc2[m]
+    assert np.median(rel2) < 0.06
+
+
+# ------------------------------------------------------------ invariants
+def test_octahedral_symmetry():
+    """Odd N (symmetric window), source at the centre: permuting axes and
+    flipping signs of field and grid leaves the solution invariant up to rounding."""
+    n, R, c = 15, 7.0, 7
+    nH = S.lognormal_field(n, 1e-3, sigma_ln=0.7, seed=11)
+    xHI = S.uniform_xhi(n, seed=12)
+    tab = O.make_table("bb")
+    base = O.raytrace(n, CELL32, nH, xHI, [[c, c, c]], [1e53], [R], tab, coldens_src=0)
+    g0 = base["gamma"].reshape(n, n, n)
+    t0 = base["coldens"].reshape(n, n, n)
+    for perm in itertools.permutations(range(3)):
+        for flips in itertools.product((False, True), repeat=3):
+            def tf(a):
+                b = np.transpose(a, perm)
+                for ax, f in enumerate(flips):
+                    if f:
+                        b = np.flip(b, axis=ax)
+                return np.ascontiguousarray(b)
+            r = O.raytrace(n, CELL32, tf(nH), tf(xHI), [[c, c, c]], [1e53], [R], tab,
+                           coldens_src=0)
+            np.testing.assert_allclose(r["coldens"].reshape(n, n, n), tf(t0), rtol=1e-13, atol=0)
+            np.testing.assert_allclose(r["gamma"].reshape(n, n, n), tf(g0), rtol=1e-9,
+                                       atol=1e-12 * g0.max())
+
+
+def test_periodic_translation_is_exact():
+    n = 16
+    nH = S.lognormal_field(n, 1e-3, seed=5)
+    xHI = S.uniform_xhi(n, seed=6)
+    tab = O.make_table("bb")
+    src = np.array([[3, 14, 9], [0, 0, 15]], dtype=np.int32)
+    ndot = np.array([1e52, 3e53])
+    R = np.array([9.0, 6.5])
+    a = O.raytrace(n, CELL32, nH, xHI, src, ndot, R, tab, coldens_src=1)
+    sh = (5, -3, 11)
+    b = O.raytrace(n, CELL32, np.roll(nH, sh, (0, 1, 2)), np.roll(xHI, sh, (0, 1, 2)),
+                   (src + np.array(sh)) % n, ndot, R, tab, coldens_src=1)
+    assert np.array_equal(np.roll(a["gamma"].reshape(n, n, n), sh, (0, 1, 2)),
+                          b["gamma"].reshape(n, n, n))
+    assert np.array_equal(np.roll(a["coldens"].reshape(n, n, n), sh, (0, 1, 2)),
+                          b["coldens"].reshape(n, n, n))
+
+
+def test_linearity_and_superposition():
+    """Rates scale with Ndot and add over sources (Sec. 2.2, last paragraph)."""
+    n = 16
+    nH = S.lognormal_field(n, 1e-3, seed=21)
+    xHI = S.uniform_xhi(n, seed=22)
+    tab = O.make_table("bb")
+    A = (np.array([[2, 3, 4]], np.int32), np.array([1e52]), np.array([6.0]))
+    B = (np.array([[10, 12, 1]], np.int32), np.array([4e53]), np.array([7.5]))
+    ga = O.raytrace(n, CELL32, nH, xHI, *A, tab)["gamma"]
+    ga2 = O.raytrace(n, CELL32, nH, xHI, A[0], 2 * A[1], A[2], tab)["gamma"]
+    assert np.array_equal(ga2, 2 * ga)
+    gb = O.raytrace(n, CELL32, nH, xHI, *B, tab)["gamma"]
+    gab = O.raytrace(n, CELL32, nH, xHI, np.concatenate([A[0], B[0]]),
+                     np.concatenate([A[1], B[1]]), np.concatenate([A[2], B[2]]), tab)["gamma"]
+    np.testing.assert_allclose(gab, ga + gb, rtol=1e-15, atol=0)
+    # threaded chunking only changes the summation order
+    many = S.catalogue(nH, 40, 1e50, 1e54, radius=5.0, seed=23)
+    g1 = O.raytrace(n, CELL32, nH, xHI, *many, tab, nthreads=1)["gamma"]
+    g4 = O.raytrace(n, CELL32, nH, xHI, *many, tab, nthreads=4)["gamma"]
+    np.testing.assert_allclose(g4, g1, rtol=1e-13, atol=0)
+    assert np.all(g1 >= 0)
+
+
+# ----------------------------------------------------- rates (Sec. 2.2)
+def test_thick_rate_on_axis_closed_form():
+    """Grey opacity, exact exponentials: Eq. sugg on the axis and in the source cell."""
+    xhi = 5e-5
+    nH = 1e-3
+    ndot = 1e54
+    r, tau, c, dt = _uniform(xhi=xhi, nH=nH, ndot=ndot)
+    g = r["gamma"].reshape(32, 32, 32)
+    nhi = nH * xhi
+    assert 0.2 < dt < 0.5
+    a = CELL32
+    for k in range(1, 16):
+        want = ndot * (math.exp(-dt * (k - 0.5)) - math.exp(-dt * (k + 0.5))) / (
+            nhi * 4 * math.pi * (k * a) ** 2 * a)
+        assert g[c, c, c + k] == pytest.approx(want, rel=1e-12)
+        assert g[c - k, c, c] == pytest.approx(want, rel=1e-12)
+    want_s = ndot * (1 - math.exp(-dt / 2)) / (nhi * a ** 3)
+    assert g[c, c, c] == pytest.approx(want_s, rel=1e-12)
+
+
+def test_photon_conservation_telescopes_along_axis():
+    """Absorptions per cell telescope: sum_k Gamma_k n_HI V_k = Ndot [g(dtau/2) - g(tau_K)]."""
+    tab = O.make_table("bb")
+    xhi, nH, ndot = 2e-5, 1e-3, 1e54
+    r, tau, c, dt = _uniform(xhi=xhi, nH=nH, ndot=ndot, tab=tab)
+    g = r["gamma"].reshape(32, 32, 32)
+    a = CELL32
+    nhi = nH * xhi
+    K = 15
+    absorbed = sum(g[c, c, c + k] * nhi * 4 * math.pi * (k * a) ** 2 * a for k in range(1, K + 1))
+    gtab = O.table_eval(tab, np.array([dt / 2, tau[c, c, c + K]]))
+    assert absorbed == pytest.approx(ndot * (gtab[0] - gtab[1]), rel=1e-12)
+    # the source cell absorbs Ndot [1 - g(dtau/2)] over n_HI alpha^3 atoms
+    g0 = O.table_eval(tab, np.array([0.0]))[0]
+    assert g[c, c, c] * nhi * a ** 3 == pytest.approx(ndot * (g0 - gtab[0]), rel=1e-12)
+
+
+def test_optically_thin_limit():
+    """Eq. gamma -> Eq. gammalocal as Delta tau -> 0 (Sec. 2.2)."""
+    a = CELL32
+    ndot = 1e54
+    # thin branch proper: dtau*ds <= tau_lim
+    r, tau, c, dt = _uniform(xhi=1e-12, ndot=ndot)
+    assert dt < O.TAU_LIM
+    g = r["gamma"].reshape(32, 32, 32)
+    for k in range(1, 16):
+        want = ndot * O.SIGMA0 * math.exp(-dt * (k - 0.5)) / (4 * math.pi * (k * a) ** 2)
+        assert g[c, c, c + k] == pytest.approx(want, rel=1e-14)
+    # thick branch with a tiny Delta tau converges to the same value
+    r, tau, c, dt = _uniform(xhi=1e-10, ndot=ndot)
+    assert O.TAU_LIM < dt < 1e-6
+    g = r["gamma"].reshape(32, 32, 32)
+    for k in range(1, 16):
+        local = ndot * O.SIGMA0 * math.exp(-dt * (k - 0.5)) / (4 * math.pi * (k * a) ** 2)
+        assert g[c, c, c + k] == pytest.approx(local, rel=1e-6)
+
+
+# ------------------------------------------------------------ tables (Eq. tables)
+def test_grey_knots_are_exponentials():
+    g, h = O.table_knots("grey")
+    t = O.knot_taus()
+    np.testing.assert_allclose(g, np.exp(-t), rtol=3e-16, atol=0)  # one ulp: libm vs numpy
+    assert np.array_equal(h, g)
+
+
+def test_blackbody_knots_match_independent_quadrature():
+    from scipy.integrate import quad
+    g, h = O.table_knots("bb", 5e4)
+    t = O.knot_taus()
+    theta = 13.6 * 1.602176634e-12 / (1.380649e-16 * 5e4)
+
+    def w(x):
+        y = theta * x
+        return x * x * math.exp(-y) / -math.expm1(-y)
+
+    norm = quad(w, 1, np.inf, epsabs=0, epsrel=1e-13, limit=500)[0]
+    for k in [0, 1, 500, 1000, 1700, 2000, 2300, 2600, 2800, len(t) - 2]:
+        tau = t[k]
+
+        def fg(x):
+            return w(x) * math.exp(-tau * x ** -O.BETA)
+
+        def fh(x):
+            return w(x) * x ** -O.BETA * math.exp(-tau * x ** -O.BETA)
+
+        # split at the saddle point of exp(-tau x^-beta - theta x)
+        xs = max(1.0, (O.BETA * tau / theta) ** (1 / (O.BETA + 1)))
+        pts = sorted({1.0, xs, 2 * xs, 4 * xs})
+        vg = sum(quad(fg, lo, hi, epsabs=0, epsrel=1e-13, limit=500)[0]
+                 for lo, hi in zip(pts[:-1], pts[1:])) + quad(fg, pts[-1], np.inf, epsabs=0,
+                                                               epsrel=1e-13, limit=500)[0]
+        vh = sum(quad(fh, lo, hi, epsabs=0, epsrel=1e-13, limit=500)[0]
+                 for lo, hi in zip(pts[:-1], pts[1:])) + quad(fh, pts[-1], np.inf, epsabs=0,
+                                                               epsrel=1e-13, limit=500)[0]
+        assert g[k] == pytest.approx(vg / norm, rel=1e-9), tau
+        assert h[k] == pytest.approx(vh / norm, rel=1e-9), tau
+    assert g[0] == pytest.approx(1.0, rel=1e-14)
+    assert np.all(np.diff(g) < 0) and np.all(h > 0)
+    # h = -dg/dtau: centred differences of the knot values
+    mid = (t[1:] + t[:-1]) / 2
+    sel = (mid > 1e-3) & (mid < 1e3)
+    dg = -np.diff(g) / np.diff(t)
+    hm = np.interp(mid, t, h)
+    np.testing.assert_allclose(dg[sel], hm[sel], rtol=2e-3)
+
+
+def test_table_lookup_is_chord_interpolation():
+    g, h = O.table_knots("bb", 5e4)
+    tab = O.Table(0, g, h)
+    t = O.knot_taus()
+    # at knots: the knot value; at the last knot and beyond: 0
+    inner = t[:-1]
+    np.testing.assert_allclose(O.table_eval(tab, inner), g[:-1], rtol=1e-13, atol=1e-300)
+    assert np.all(O.table_eval(tab, np.array([2.0 ** 14, 1e5, np.inf])) == 0.0)
+    # random taus: chord between the bracketing knots (segment located with searchsorted)
+    rng = np.random.default_rng(0)
+    x = np.concatenate([10 ** rng.uniform(-12, 4.2, 4000), rng.uniform(0, 2 ** -30, 50)])
+    x = x[x < 2.0 ** 14]
+    j = np.searchsorted(t, x, side="right") - 1
+    want = g[j] + (g[j + 1] - g[j]) * (x - t[j]) / (t[j + 1] - t[j])
+    np.testing.assert_allclose(O.table_eval(tab, x), want, rtol=1e-11, atol=1e-300)
+    wh = h[j] + (h[j + 1] - h[j]) * (x - t[j]) / (t[j + 1] - t[j])
+    np.testing.assert_allclose(O.table_eval(tab, x, "h"), wh, rtol=1e-11, atol=1e-300)
+
+
+# ------------------------------------------------------------ chemistry (Sec. 2.1)
+def _rk4_traj(x0, G, ne, C, al, dt, steps=4000):
+    """Brute-force RK4 of Eq. chemistry with n_e held fixed; returns x(dt) and <x>."""
+    def f(x):
+        return (1 - x) * (G + ne * C) - x * ne * al
+    h = dt / steps
+    xs = [x0]
+    x = x0
+    for _ in range(steps):
+        k1 = f(x)
+        k2 = f(x + h / 2 * k1)
+        k3 = f(x + h / 2 * k2)
+        k4 = f(x + h * k3)
+        x = x + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        xs.append(x)
+    xs = np.array(xs)
+    avg = (xs[0] + xs[-1] + 4 * xs[1:-1:2].sum() + 2 * xs[2:-1:2].sum()) * h / 3 / dt
+    return x, avg
+
+
+def test_chemistry_matches_ode_and_limits():
+    rng = np.random.default_rng(3)
+    nH = 10 ** rng.uniform(-4, -2, 6)
+    x0 = np.array([0.0, 1e-3, 0.3, 0.9, 1.0, 0.5])
+    G = np.array([1e-12, 3e-14, 0.0, 1e-13, 0.0, 5e-15])
+    dt = 5.0 * S.MYR_S
+    al, C = 2.59e-13, 1e-16
+    xa, xn, _ = O.chemistry(nH, x0, x0, G, dt, alpha_H=al, C_H=C, tol=1e-13, maxit=200)
+    for c in range(6):
+        ne = nH[c] * xa[c]
+        x_end, avg = _rk4_traj(x0[c], G[c], ne, C, al, dt)
+        assert xn[c] == pytest.approx(x_end, rel=1e-9, abs=1e-15)
+        assert xa[c] == pytest.approx(avg, rel=1e-9, abs=1e-15)
+    # no radiation, no collisions, fully neutral: nothing happens
+    xa, xn, _ = O.chemistry([1e-3], [0.0], [0.0], [0.0], dt, C_H=0.0)
+    assert xa[0] == 0.0 and xn[0] == 0.0
+    # very long step: equilibrium x_eq = (G + ne C)/(G + ne (C + alpha))
+    xa, xn, _ = O.chemistry([1e-3], [0.0], [0.0], [1e-12], 1e6 * dt, C_H=0.0, tol=1e-14, maxit=500)
+    ne = 1e-3 * xa[0]
+    assert xn[0] == pytest.approx(1e-12 / (1e-12 + ne * al), rel=1e-9)
+
+
+# ------------------------------------------------------------ Stromgren (Sec. 4.1.1)
+def _golden():
+    with open(os.path.join(HERE, "golden", "stromgren_test1.json")) as f:
+        return json.load(f)
+
+
+def test_stromgren_constants_match_paper():
+    gd = _golden()
+    inp, pr = gd["inputs"], gd["printed"]
+    t_rec = 1.0 / (inp["alpha_H_cm3_s"] * inp["n_H_cm3"]) / S.MYR_S
+    r_S = (3 * inp["Ndot_s"] / (4 * math.pi * inp["alpha_H_cm3_s"] * inp["n_H_cm3"] ** 2)) ** (
+        1 / 3) / S.KPC_CM
+    assert abs(t_rec - pr["t_rec_Myr"]) < gd["printed_precision"]["t_rec_Myr"]
+    assert abs(r_S - pr["r_S_kpc"]) < gd["printed_precision"]["r_S_kpc"]
+
+
+def stromgren_run(n=32, dt_myr=50.0, t_end_myr=500.0, max_iter=30):
+    """Test 1 (Sec. 4.1.1) with the oracle: grey source in a uniform box, RT <-> chemistry."""
+    gd = _golden()["inputs"]
+    box = gd["box_kpc"] * S.KPC_CM
+    cell = box / n
+    c = n // 2
+    nH = np.full(n ** 3, gd["n_H_cm3"])
+    x = np.zeros(n ** 3)  # x_HII
+    tab = O.make_table("grey_exact")
+    dt = dt_myr * S.MYR_S
+    out = []
+    t = 0.0
+    while t < t_end_myr * S.MYR_S - 1e-6 * dt:
+        xa = x.copy()
+        for it in range(max_iter):
+            G = O.raytrace(n, cell, nH, 1.0 - xa, [[c, c, c]], [gd["Ndot_s"]], [n / 2.0 - 0.5],
+                           tab)["gamma"]
+            xa_new, xn, unconv = O.chemistry(nH, x, xa, G, dt, alpha_H=gd["alpha_H_cm3_s"])
+            xa = xa_new
+            if unconv < 1e-4 * n ** 3 and it > 0:
+                break
+        x = xn
+        t += dt
+        # I-front along +x: x_HI = 0.5 by linear interpolation between cell centres
+        xhi = 1.0 - x.reshape(n, n, n)[c:, c, c]
+        k = int(np.argmax(xhi > 0.5))
+        r = (k - 1 + (0.5 - xhi[k - 1]) / (xhi[k] - xhi[k - 1])) * cell if k > 0 else 0.0
+        out.append((t, r))
+    return out
+
+
+def test_stromgren_ifront_radius():
+    """I-front radius vs r_S [1 - exp(-t/t_rec)]^(1/3) (Eq. rI1); the paper finds at most
+    a ~6 % overshoot at t >~ t_rec.  Coarse 32^3 grid (r_S ~ 10 cells), coarse step."""
+    gd = _golden()["inputs"]
+    al, n0, nd = gd["alpha_H_cm3_s"], gd["n_H_cm3"], gd["Ndot_s"]
+    t_rec = 1.0 / (al * n0)
+    r_S = (3 * nd / (4 * math.pi * al * n0 ** 2)) ** (1 / 3)
+    for t, r in stromgren_run():
+        ana = r_S * (1 - math.exp(-t / t_rec)) ** (1 / 3)
+        assert 0.95 < r / ana < 1.07, (t / S.MYR_S, r / ana)
+
+
+# ------------------------------------------------ derivatives of the oracle
+def test_complex_step_matches_finite_differences():
+    n = 12
+    nH = S.lognormal_field(n, 1e-3, sigma_ln=0.5, seed=31).reshape(-1)
+    xHI = np.full(n ** 3, 1e-4)  # tau per cell ~ O(0.1..1): rates over many cells
+    cell = 10.0 * S.KPC_CM
+    pos = np.array([[2, 3, 4], [6, 6, 6], [10, 1, 7]], np.int32)
+    ndot = np.array([1e50, 3e50, 2e49])
+    R = np.array([5.0, 4.5, 6.0])
+    w = S.loss_weights(n ** 3)
+    tab = O.make_table("grey_exact")
+
+    def loss(nh):  # exactly rounded sum, so that FD differences carry no summation noise
+        return math.fsum(w * O.raytrace(n, cell, nh, xHI, pos, ndot, R, tab)["gamma"])
+
+    cells = np.array([((6 * n) + 6) * n + 7, ((2 * n) + 3) * n + 4, ((6 * n) + 5) * n + 6,
+                      ((1 * n) + 2) * n + 3], np.int64)
+    dn, dq = O.loss_grad_cs(n, cell, nH, xHI, pos, ndot, R, tab, w, cells, np.arange(3))
+    h = 1e-6
+    for t, cidx in enumerate(cells):
+        up = nH.copy()
+        dn_ = nH.copy()
+        up[cidx] *= math.exp(h)
+        dn_[cidx] *= math.exp(-h)
+        fd = (loss(up) - loss(dn_)) / (2 * h)
+        assert dn[t] == pytest.approx(fd, rel=1e-6, abs=1e-9 * abs(loss(nH)))
+    # dL/dlog Ndot_s = sum_p w_p Gamma_sp  (linearity in Ndot)
+    for s in range(3):
+        Ls = O.raytrace(n, cell, nH, xHI, pos[s:s + 1], ndot[s:s + 1], R[s:s + 1], tab,
+                        gamma=False, wloss=w)["loss"]
+        assert dq[s] == pytest.approx(Ls, rel=1e-12)
