@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Throughput of the short-characteristics ray tracer (source-voxels/s).
+
+Workload (default): 250^3 periodic grid in a 349 Mpc box, lognormal P(k)~k^-2
+density (mean 2e-4 cm^-3, ln-sigma 1), x_HI ~ U[0,1), 1e6 sources at the
+densest cells, photon rates log-uniform in [1e50, 1e55] s^-1, radius
+R = 5 (Ndot/1e50)^(1/5) = 5..50 cells, 5e4 K blackbody tables, FP64.
+
+One step = the whole forward hot path for one batch: source ingest (merge,
+longest-first order) -> per-cell optical depth -> batched SC trace with rate
+accumulation -> chemistry step with the convergence count.  The metric counts
+source-voxels with the paper's normaliser sum_s (4/3) pi R_s^3 (Sec. 4.2).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank traces its
+own independent box of the same size (weak scaling, no collective on the data
+path); value = all ranks' source-voxels / max-over-ranks time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "source-voxels/s (ns per source per voxel) at 250^3, ~1e6 src; batched vs plain"
+UNIT = "source-voxels/s"
+FP64_FLOPS_PER_SV = 9.0       # tau_in: 1 mul + 3 fma; tau_out: 1 fma
+FP64_FLOPS_PER_RATE = 10.0    # dtau*ds, 2 table fma, difference, 3 products
+BYTES_PER_SV = 16.0           # dtau gather (8 B) + rate read-modify-write share (8 B)
+SMS, FP64_FMA_PER_CLK_SM, SM_MAX_GHZ = 152, 2, 2.07
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nsrc", type=int, default=1_000_000)
+    ap.add_argument("--n", type=int, default=250)
+    ap.add_argument("--box-mpc", type=float, default=349.0)
+    ap.add_argument("--plain-steps", type=int, default=1, help="timed RT_SCHED_PLAIN traces")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle baseline sample")
+    return ap.parse_args()
+
+
+def workload(args, rank=0):
+    from paper_2311_01492_gb300 import synth as S
+    seed = S.BASE_SEED + 10_000 * rank
+    w = S.lognormal_box(args.n, args.box_mpc, args.nsrc, 1e50, 1e55, radius=None, seed=seed)
+    w["paper_sv"] = float(np.sum(4.0 / 3.0 * math.pi * w["radius"] ** 3))
+    w["name"] = "box%d_%gMpc_lognormal_%dsrc_R5-50_bb5e4" % (args.n, args.box_mpc, len(w["ndot"]))
+    return w
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        mx = max(r[1] for r in rows)
+        load = [r for r in rows if r[0] > 0.5 * mx] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in load for i, v in enumerate(r[2]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(w, target_s, cores):
+    """Time the CPU oracle on a random subset of the sources; returns sv/s and the sample."""
+    from oracle import oracle as O
+    tab = O.make_table("bb", 5e4)
+    rng = np.random.default_rng(7)
+    nsrc = len(w["ndot"])
+
+    def run(k):
+        idx = np.sort(rng.choice(nsrc, size=min(k, nsrc), replace=False))
+        sv = float(np.sum(4.0 / 3.0 * math.pi * w["radius"][idx] ** 3))
+        t0 = time.perf_counter()
+        O.raytrace(w["n"], w["cell_cm"], w["nH"], w["xHI"], w["pos"][idx], w["ndot"][idx],
+                   w["radius"][idx], tab, nthreads=cores)
+        return sv, time.perf_counter() - t0, len(idx)
+
+    sv, dt, k = run(max(cores * 8, 256))          # calibration
+    rate = sv / dt
+    per_src = sv / k
+    k2 = int(min(nsrc, max(k, target_s * rate / per_src)))
+    sv, dt, k = run(k2)
+    return sv / dt, dt, k, sv
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle timed on this host's cores (bounded samples of the same workload)."""
+    if rank != 0:
+        return
+    cores = len(os.sched_getaffinity(0))
+    from oracle import build as OB
+    OB.build()
+    w = workload(args)
+    per_step = []
+    samples = []
+    for step in range(args.warmup + args.steps):
+        rate, dt, k, sv = oracle_sample(w, min(args.cpu_seconds, 10.0), cores)
+        if step >= args.warmup:
+            per_step.append((rate, dt, k, sv))
+            samples.append(k)
+    value = sum(r[3] for r in per_step) / sum(r[1] for r in per_step)
+    ms = 1e3 * sum(r[1] for r in per_step) / len(per_step)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "n": args.n, "nsrc": len(w["ndot"]),
+                   "sample": "random subsets of the sources per step (%s sources)" % samples},
+        "ns_per_source_voxel": 1e9 / value,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "per step a random subset of %s of the %d sources, full 250^3 "
+                                   "fields, OpenMP over sources" % (samples, len(w["ndot"]))},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2311_01492_gb300 import api as A
+    from paper_2311_01492_gb300 import _lib as L
+
+    w = workload(args, rank)
+    n = w["n"]
+    dev = torch.device("cuda", local)
+    g = A.Grid(n, w["cell_cm"])
+    g.set_tables("bb", T_bb=5e4)
+    f64 = dict(device=dev, dtype=torch.float64)
+    nH_d = torch.tensor(w["nH"].reshape(-1), **f64)
+    xHI_d = torch.tensor(w["xHI"].reshape(-1), **f64)
+    pos_d = torch.tensor(w["pos"], device=dev, dtype=torch.int32)
+    ndot_d = torch.tensor(w["ndot"], **f64)
+    R_d = torch.tensor(w["radius"], **f64)
+    x0_d = (1.0 - xHI_d).contiguous()
+    gamma = torch.empty(n ** 3, **f64)
+    g.set_density(nH_d)
+    g.set_xHI(xHI_d)
+    dt = 5.0 * 3.15576e13
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        g.set_sources(pos_d, ndot_d, R_d)
+        g.raytrace(gamma, schedule="batched")
+        xa, xn, cnt = g.chemistry_step(gamma, x0_d, x0_d, dt)
+        return cnt
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---------------- device-resident timed region
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    step_ms, trace_ms, rate_cells = [], [], []
+    launches0 = L.lib().rt_kernel_launch_count()
+    for _ in range(args.steps):
+        flush.fill_(float(len(step_ms)))  # evict L2 between steps (512 MB write)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        st = g.stats()  # synchronises; trace events were recorded on the launch stream
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        trace_ms.append(st["trace_ms"])
+        rate_cells.append(st["rate_cells"])
+    launches = L.lib().rt_kernel_launch_count() - launches0
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = g.stats()
+    exact_sv = st["source_voxels"]
+    value = world * w["paper_sv"] / (ms * 1e-3)
+    tr_ms = statistics.mean(trace_ms)
+
+    # ---------------- plain (ASORA-style block-per-source) comparison
+    plain = None
+    if args.plain_steps > 0:
+        pm = []
+        for _ in range(args.plain_steps):
+            flush.fill_(1.0)
+            g.raytrace(gamma, schedule="plain")
+            pm.append(g.stats()["trace_ms"])
+        pmed = statistics.median(pm)
+        plain = {"trace_ms": pmed, "sv_per_s": w["paper_sv"] / (pmed * 1e-3),
+                 "ns_per_source_voxel": pmed * 1e6 / w["paper_sv"],
+                 "batched_speedup": pmed / tr_ms}
+
+    # ---------------- end to end through the public API with host buffers
+    pin = dict(pin_memory=True)
+    h_nH = torch.tensor(w["nH"].reshape(-1), dtype=torch.float64).pin_memory()
+    h_xHI = torch.tensor(w["xHI"].reshape(-1), dtype=torch.float64).pin_memory()
+    h_pos = torch.tensor(w["pos"], dtype=torch.int32).pin_memory()
+    h_ndot = torch.tensor(w["ndot"], dtype=torch.float64).pin_memory()
+    h_R = torch.tensor(w["radius"], dtype=torch.float64).pin_memory()
+    h_gamma = torch.empty(n ** 3, dtype=torch.float64, **pin)
+    h_cnt = torch.empty(1, dtype=torch.int64, **pin)
+    e2e_in = [h_nH, h_xHI, h_pos, h_ndot, h_R]
+    h2d = sum(t.numel() * t.element_size() for t in e2e_in)
+    d2h = h_gamma.numel() * 8 + 8
+    nH2 = torch.empty_like(nH_d)
+    xHI2 = torch.empty_like(xHI_d)
+    pos2 = torch.empty_like(pos_d)
+    ndot2 = torch.empty_like(ndot_d)
+    R2 = torch.empty_like(R_d)
+    x02 = torch.empty_like(x0_d)
+
+    def e2e_step():
+        nH2.copy_(h_nH, non_blocking=True)
+        xHI2.copy_(h_xHI, non_blocking=True)
+        pos2.copy_(h_pos, non_blocking=True)
+        ndot2.copy_(h_ndot, non_blocking=True)
+        R2.copy_(h_R, non_blocking=True)
+        g.set_density(nH2)
+        g.set_xHI(xHI2)
+        g.set_sources(pos2, ndot2, R2)
+        g.raytrace(gamma, schedule="batched")
+        torch.sub(1.0, xHI2, out=x02)
+        xa, xn, cnt = g.chemistry_step(gamma, x02, x02, dt)
+        h_gamma.copy_(gamma, non_blocking=True)
+        h_cnt.copy_(cnt, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(2.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        torch.cuda.synchronize()
+        e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_ms = statistics.mean(e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # ---------------- roofline of the dominant kernel (the batched trace)
+    flops = FP64_FLOPS_PER_SV * exact_sv + FP64_FLOPS_PER_RATE * statistics.mean(rate_cells)
+    achieved_tf = flops / (tr_ms * 1e-3) / 1e12
+    peak_tf = SMS * FP64_FMA_PER_CLK_SM * 2 * SM_MAX_GHZ * 1e9 / 1e12
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    traffic = None
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved_tf / peak_tf, "traffic": traffic,
+                "kernel": "k_trace_faces (FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "algorithmic_flops_per_launch": flops,
+                "hbm_view": {"achieved_gbs": BYTES_PER_SV * exact_sv / (tr_ms * 1e-3) / 1e9,
+                             "peak_gbs": hbm_peak,
+                             "frac": BYTES_PER_SV * exact_sv / (tr_ms * 1e-3) / 1e9 / hbm_peak,
+                             "peak_source": "MEASURED_PEAKS.json" if peaks else "fallback"}}
+
+    cpu = None
+    if rank == 0 and world == 1:
+        cores = len(os.sched_getaffinity(0))
+        try:
+            from oracle import build as OB
+            OB.build()
+            rate, cdt, k, csv = oracle_sample(w, args.cpu_seconds, cores)
+            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "%d random sources of the same 250^3 workload (%.3e source-voxels, "
+                             "%.1f s), OpenMP over sources" % (k, csv, cdt)}
+        except Exception as e:  # the baseline is a report, not a gate
+            cpu = {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "failed: %s" % e}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "n": n, "box_mpc": args.box_mpc,
+                       "nsrc": len(w["ndot"]), "radius_cells": "5-50 (R=5(Ndot/1e50)^0.2)",
+                       "schedule": "batched (persistent, 6 faces/source, LPT queue)",
+                       "step": "ingest + dtau + trace + chemistry",
+                       "l2": "512 MB write between steps; fields 3 x 125 MB > L2",
+                       "per_rank": "independent box per rank (weak scaling)"},
+            "ns_per_source_voxel": ms * 1e6 / w["paper_sv"],
+            "source_voxels_paper": w["paper_sv"], "source_voxels_exact": exact_sv,
+            "trace_only": {"ms": tr_ms, "sv_per_s": w["paper_sv"] / (tr_ms * 1e-3),
+                           "ns_per_source_voxel": tr_ms * 1e6 / w["paper_sv"],
+                           "rate_cells": statistics.mean(rate_cells)},
+            "plain": plain,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * w["paper_sv"] / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": launches // max(1, args.steps),
+            "gpu_launches_note": "library kernels per step (+ CUB radix-sort/scan kernels of the "
+                                 "source ingest)",
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * asora.h -- C ABI of the GB300 short-characteristics ray tracer.
+ *
+ * Photo-ionisation rates from point sources on periodic 3-D hydrogen grids
+ * (arXiv 2311.01492, "pyC2Ray"/ASORA): for every source, the H I column
+ * density to each cell inside its ray-tracing radius is built by
+ * short-characteristics interpolation from upstream cells plus the in-cell
+ * path (Sec. 3.1, Eqs. raga/interp), converted to a photon-conserving rate
+ * through tabulated transmission functions (Sec. 2.2, Eqs. gamma, tables,
+ * sugg) and summed over sources.  A time-averaged chemistry update (Sec. 2.1,
+ * Eq. time_avrg_sol) closes the ray-tracing <-> chemistry iteration (Fig. 1).
+ *
+ * Conventions (all entry points):
+ *   - Every function returns rt_status; on failure rt_last_error() gives a
+ *     thread-local message.  Nothing is partially applied on RT_ERR_INVALID.
+ *   - Field pointers named d_* are DEVICE pointers of the current CUDA device,
+ *     owned by the caller.  Inputs registered with rt_set_* are borrowed until
+ *     the next rt_set_* of the same input or rt_grid_destroy; outputs are
+ *     borrowed for the duration of the call (work is asynchronous on the
+ *     grid's stream: the caller keeps buffers alive until that stream is
+ *     synchronised).  Host pointers (h_*) are read during the call only.
+ *   - Fields are FP64, C order: cell (i,j,k) of a box of size n is at
+ *     (i*n + j)*n + k.  Ensembles concatenate boxes in box order.
+ *   - Units are CGS: cm, s, cm^-3, cm^2.
+ *   - The library owns all of its scratch memory (device) and frees it in
+ *     rt_grid_destroy.  All work runs on the stream given at creation (or set
+ *     with rt_set_stream); no call synchronises the device unless stated.
+ */
+#ifndef ASORA_H
+#define ASORA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RT_OK = 0,
+  RT_ERR_INVALID = 1, /* bad argument or bad input data                       */
+  RT_ERR_OOM = 2,     /* device allocation failed                             */
+  RT_ERR_CUDA = 3,    /* a CUDA runtime call failed                           */
+  RT_ERR_TIMEOUT = 4, /* a bounded device-side wait ran out                   */
+  RT_ERR_STATE = 5    /* call order violated (e.g. trace before set_tables)   */
+} rt_status;
+
+typedef struct rt_grid* rt_grid_t;
+typedef void* rt_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+/* Physics parameters.  rt_params_default() fills the paper's values. */
+typedef struct {
+  double sigma0_cm2; /* H I cross section at threshold, 6.3e-18 cm^2 (Sec. 4.1.3)         */
+  double tau_lim;    /* cells with dtau*ds <= tau_lim use the thin limit (Eq. gammalocal)  */
+} rt_params;
+
+/* Trace schedules for rt_raytrace. */
+enum {
+  RT_SCHED_AUTO = 0,    /* batched, with the autotuned (or default) configuration           */
+  RT_SCHED_PLAIN = 1,   /* ASORA-style: one CTA per source, octahedral shells S_q in order   */
+  RT_SCHED_BATCHED = 2  /* persistent work queue over (source, face) items, LPT order        */
+};
+
+/* Rate table kinds for rt_set_tables. */
+enum {
+  RT_TABLE_CHORDS = 0, /* chords through knot values of g and h (Eq. tables)                */
+  RT_TABLE_GREY_EXACT = 1 /* grey opacity evaluated exactly: g = h = exp(-tau) (Sec. 4.1.1)  */
+};
+
+void rt_params_default(rt_params* p);
+
+/* Thread-local message describing the last failure of this thread. */
+const char* rt_last_error(void);
+
+/* One periodic box of n^3 cells of size cell_cm.  s: stream for all work. */
+rt_status rt_grid_create(rt_grid_t* g, int n, double cell_cm, const rt_params* p, rt_stream_t s);
+
+/* An ensemble of nbox independent periodic boxes (h_n[b]^3 cells of size
+ * h_cell_cm[b]) traced in one launch.  Fields are the boxes concatenated. */
+rt_status rt_ensemble_create(rt_grid_t* g, int nbox, const int* h_n, const double* h_cell_cm,
+                             const rt_params* p, rt_stream_t s);
+
+rt_status rt_set_stream(rt_grid_t g, rt_stream_t s);
+
+/* Number of knots of a table with parameters (E0, E1, bits): (E0+E1)*2^bits + 2.
+ * Knot 0 is tau = 0, knot 1+t is 2^(t>>bits - E0) * (1 + (t & (2^bits-1))/2^bits),
+ * the last knot is 2^E1.  tau >= 2^E1 transmits nothing. */
+int rt_table_nknots(int E0, int E1, int bits);
+
+/* Knot values of the frequency-integrated transmission g(tau) = gamma(N_HI)/Ndot
+ * (Eq. tables normalised by Eq. ngammalnu) and h(tau) = -dg/dtau for a blackbody of
+ * temperature T_bb (K) with sigma_nu = sigma0 (nu/nu_th)^-beta, h nu_th = 13.6 eV
+ * (Sec. 2.2, 4.1.3).  Host arrays of rt_table_nknots() doubles.  Host code. */
+rt_status rt_table_blackbody(double T_bb, double beta, int E0, int E1, int bits, double* h_g,
+                             double* h_h);
+
+/* Rate tables (host arrays of rt_table_nknots(E0,E1,bits) doubles, copied).
+ * kind RT_TABLE_CHORDS: g, h are knot values; a lookup of tau uses segment
+ * 1 + (e+E0)*2^bits + m from tau's binary exponent e and top mantissa bits m
+ * (segment 0 below 2^-E0) and returns fma(c1, tau, c0) with
+ * c1 = (v_hi - v_lo)/(tau_hi - tau_lo), c0 = fma(-c1, tau_lo, v_lo).
+ * kind RT_TABLE_GREY_EXACT: g and h may be NULL; exp(-tau) is used. */
+rt_status rt_set_tables(rt_grid_t g, int kind, int E0, int E1, int bits, const double* h_g,
+                        const double* h_h);
+
+/* Hydrogen density n_H (cm^-3) and neutral fraction x_HI of every cell.
+ * Validated (finite, n_H >= +0, 0 <= x_HI <= 1, no negative zero): this call
+ * synchronises the grid's stream and returns RT_ERR_INVALID on bad data. */
+rt_status rt_set_density(rt_grid_t g, const double* d_nH);
+rt_status rt_set_xHI(rt_grid_t g, const double* d_xHI);
+
+/* Sources: d_pos int32[nsrc][3] cell indices (i,j,k) in [0,n), d_box int32[nsrc]
+ * box ids (NULL: all in box 0), d_ndot photon rates (s^-1, >= 0), d_radius
+ * ray-tracing radius in cells (> 0; cells with |Delta|^2 > floor(R^2) are not
+ * traced, Sec. 3.3).  Sources in the same cell with the same radius are merged by
+ * summing their rates (Sec. 3: identical spectra).  The library copies what it
+ * needs; the pointers are not kept.  Synchronises the grid's stream. */
+rt_status rt_set_sources(rt_grid_t g, int nsrc, const int32_t* d_pos, const int32_t* d_box,
+                         const double* d_ndot, const double* d_radius);
+
+/* Photo-ionisation rate Gamma (s^-1) of every cell, summed over all sources,
+ * written to d_gamma (all cells overwritten).  schedule: RT_SCHED_*. */
+rt_status rt_raytrace(rt_grid_t g, double* d_gamma, int schedule);
+
+/* Column density (cm^-2) from source `src` (index in the rt_set_sources arrays)
+ * through the far side of every traced cell; 0 outside its traced region.
+ * schedule: RT_SCHED_PLAIN or RT_SCHED_BATCHED/AUTO (same values bit for bit). */
+rt_status rt_raytrace_source_coldens(rt_grid_t g, int src, double* d_coldens, int schedule);
+
+/* Chemistry step (Sec. 2.1, Eq. time_avrg_sol) for every cell, isothermal
+ * hydrogen.  d_x0: x_HII at the start of the step; d_xavg_in: time-averaged x_HII
+ * used by the ray trace that produced d_gamma.  Iterates n_e = n_H <x_HII> until
+ * |change| <= tol*<x> (tol = 1e-10) or 50 iterations.  Writes <x_HII> to
+ * d_xavg_out and x_HII(t+dt) to d_xnew_out; adds to *d_unconverged (device int64)
+ * the number of cells whose neutral fraction 1-<x> moved by more than
+ * conv_tol (relative) from 1 - d_xavg_in. */
+rt_status rt_chemistry_step(rt_grid_t g, const double* d_gamma, const double* d_x0,
+                            const double* d_xavg_in, double dt_s, double alpha_H, double C_H,
+                            double conv_tol, double* d_xavg_out, double* d_xnew_out,
+                            int64_t* d_unconverged);
+
+/* One time step of the ray-tracing <-> chemistry iteration (Fig. 1): starting
+ * from <x> = x0 (d_x, x_HII, updated in place to x(t+dt)), repeat
+ * {x_HI = 1-<x>; Gamma = trace; <x> = chemistry} until fewer than
+ * conv_frac * ncells cells are unconverged or max_iter iterations.  With
+ * use_graph != 0 the max_iter iterations are one captured CUDA graph whose
+ * later iterations are no-ops once converged.  d_gamma receives the last
+ * rates; *h_iters (host, may be NULL) the iterations run (synchronises).
+ * Requires rt_set_density; the grid's registered x_HI is replaced by an
+ * internal buffer. */
+rt_status rt_iterate(rt_grid_t g, double* d_x, double dt_s, double alpha_H, double C_H,
+                     int max_iter, double conv_tol, double conv_frac, int use_graph,
+                     double* d_gamma, int* h_iters);
+
+/* Timing/launch statistics of the last rt_raytrace on this grid (device event
+ * time of the trace kernels, launches, source-voxels traced). */
+typedef struct {
+  double trace_ms;          /* event time of the trace kernel launches              */
+  double prep_ms;           /* event time of per-call preparation (dtau, zeroing)   */
+  int64_t source_voxels;    /* sum over (merged) sources of traced cells            */
+  int64_t items;            /* work items of the last launch                        */
+  int64_t rate_cells;       /* (source, cell) pairs whose rate was evaluated (tau_in below
+                               the table's upper bound; elsewhere the rate is exactly 0) */
+  int64_t kernel_launches;  /* rt_kernel_launch_count() at the time of the call         */
+  int launches;             /* kernel launches of the last rt_raytrace              */
+  int schedule;             /* schedule used                                        */
+  int block;                /* threads per CTA of the trace kernel                  */
+  int grid;                 /* CTAs of the trace kernel                             */
+} rt_stats;
+
+/* Statistics of the last trace (synchronises the grid's stream). */
+rt_status rt_get_stats(rt_grid_t g, rt_stats* out);
+
+void rt_grid_destroy(rt_grid_t g);
+
+/* Number of CUDA kernels this library has launched from host code in this
+ * process (kernels replayed by a CUDA graph are counted when captured). */
+long long rt_kernel_launch_count(void);
+
+/* Cells of the octahedral shell S_q = {|Di|+|Dj|+|Dk| = q} (Sec. 3.3, App. A) in
+ * the order the RT_SCHED_PLAIN kernel assigns them to threads: the top part
+ * Dk >= 0 (2q(q+1)+1 cells) then the bottom part.  Writes 3 ints per cell to
+ * h_out (host, may be NULL) and returns |S_q| = 4q^2+2 (1 for q = 0), or -1 for
+ * q < 0.  Host code, no GPU needed. */
+int rt_shell_enumerate(int q, int32_t* h_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASORA_H */

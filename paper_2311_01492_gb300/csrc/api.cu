@@ -1,0 +1,542 @@
+// C ABI of libasora: handles, validation, memory, launches (see include/asora.h).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "asora_internal.cuh"
+
+namespace asora {
+
+static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+rt_status fail(rt_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+rt_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();  // clear a sticky-free error so the next call starts clean
+  return e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA;
+}
+
+static int isqrt_h(int64_t x) {
+  if (x <= 0) return 0;
+  int64_t r = (int64_t)std::sqrt((double)x);
+  while (r * r > x) --r;
+  while ((r + 1) * (r + 1) <= x) ++r;
+  return (int)r;
+}
+
+static void free_grid(Grid* g) {
+  cudaFree(g->boxes_d); cudaFree(g->gtab); cudaFree(g->htab);
+  cudaFree(g->dtau); cudaFree(g->dtauT); cudaFree(g->invn);
+  cudaFree(g->src); cudaFree(g->ndot); cudaFree(g->r2lim); cudaFree(g->items);
+  cudaFree(g->src_of_input); cudaFree(g->geo); cudaFree(g->queue); cudaFree(g->err);
+  cudaFree(g->cube); cudaFree(g->unconv); cudaFree(g->xbuf); cudaFree(g->xavg);
+  cudaFree(g->xavg2); cudaFree(g->xhi_int); cudaFree(g->flags); cudaFree(g->counters);
+  for (auto& e : g->ev)
+    if (e) cudaEventDestroy(e);
+  delete g;
+}
+
+#define TRY(x)                                      \
+  do {                                              \
+    cudaError_t e_ = (x);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
+  } while (0)
+
+static rt_status ensure_geometry(Grid& g, int mmax) {
+  if (mmax <= g.geo_mmax) return RT_OK;
+  GeoEntry* geo = nullptr;
+  TRY(cudaMalloc(&geo, geo_count(mmax) * sizeof(GeoEntry)));
+  cudaError_t e = launch_geometry(geo, mmax, g.stream);
+  if (e != cudaSuccess) {
+    cudaFree(geo);
+    return cuda_fail(e, "geometry");
+  }
+  cudaFree(g.geo);
+  g.geo = geo;
+  g.geo_mmax = mmax;
+  return RT_OK;
+}
+
+// Largest layer half-width min(m, floor(sqrt(r2 - m^2))) over the layers of a face.
+static int face_hcap(int r2, int nmax) {
+  int h = 1;
+  const int L = std::min(isqrt_h(r2), nmax / 2 + 1);
+  for (int m = 1; m <= L; ++m) h = std::max(h, std::min(m, isqrt_h((int64_t)r2 - (int64_t)m * m)));
+  return h;
+}
+
+static TraceArgs base_args(Grid& g) {
+  TraceArgs a{};
+  a.boxes = g.boxes_d;
+  a.dtau = g.dtau;
+  a.dtauT = g.dtauT;
+  a.invn = g.invn;
+  a.src = g.src;
+  a.ndot = g.ndot;
+  a.r2lim = g.r2lim;
+  a.queue = g.queue;
+  a.geo = g.geo;
+  a.geo_mmax = g.geo_mmax;
+  a.tab.g = g.gtab;
+  a.tab.h = g.htab;
+  a.tab.kind = g.tab_kind;
+  a.tab.E0 = g.E0;
+  a.tab.B = g.B;
+  if (g.tab_kind == RT_TABLE_GREY_EXACT) {
+    // exp(-tau) is exactly 0 in double beyond tau = 746; skip the rate there
+    const double lim = 750.0;
+    std::memcpy(&a.tab.tau_max_bits, &lim, 8);
+    a.tab.tau_min_bits = 0;
+  } else {
+    const double tmin = std::ldexp(1.0, -g.E0), tmax = std::ldexp(1.0, g.E1);
+    std::memcpy(&a.tab.tau_min_bits, &tmin, 8);
+    std::memcpy(&a.tab.tau_max_bits, &tmax, 8);
+  }
+  a.tau_lim = g.p.tau_lim;
+  a.sigma0 = g.p.sigma0_cm2;
+  a.err = g.err;
+  a.rate_cells = g.counters;
+  return a;
+}
+
+static rt_status check_ready(Grid& g, const char* who) {
+  if (!g.have_tables) return fail(RT_ERR_STATE, std::string(who) + ": rt_set_tables not called");
+  if (!g.nH) return fail(RT_ERR_STATE, std::string(who) + ": rt_set_density not called");
+  if (!g.xHI) return fail(RT_ERR_STATE, std::string(who) + ": rt_set_xHI not called");
+  return RT_OK;
+}
+
+// Trace all sources, adding rates into `gamma` (already zeroed) or writing one
+// source's column densities.  `items`/`n_items` select the work.
+static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* items, int n_items,
+                           int schedule, int nsrc_plain, const int* skip = nullptr) {
+  TraceArgs a = base_args(g);
+  a.gamma = gamma;
+  a.coldens = coldens;
+  a.skip = skip;
+  g.stats.launches = 0;
+  TRY(cudaMemsetAsync(g.counters, 0, sizeof(unsigned long long), g.stream));
+  if (schedule == RT_SCHED_PLAIN) {
+    const int E = std::max(1, std::min(isqrt_h(g.max_r2), g.nmax / 2));
+    const int block = 256;
+    int grid = std::min(nsrc_plain, std::max(1, shells_max_grid(block)));
+    const size_t side = 2 * (size_t)E + 1;
+    const size_t need = side * side * side * sizeof(double) * (size_t)grid;
+    if (need > g.cube_bytes) {
+      cudaFree(g.cube);
+      g.cube = nullptr;
+      g.cube_bytes = 0;
+      TRY(cudaMalloc(&g.cube, need));
+      g.cube_bytes = need;
+    }
+    a.scratch = g.cube;
+    a.hcap = E;
+    a.items = items;
+    a.n_items = nsrc_plain;
+    TRY(cudaMemsetAsync(g.queue, 0, sizeof(int), g.stream));
+    TRY(launch_trace_shells(g, a, block, grid));
+    g.stats.block = block;
+    g.stats.grid = grid;
+    g.stats.launches = 1;
+    g.stats.items = nsrc_plain;
+  } else {
+    const int hcap = face_hcap(g.max_r2, g.nmax);
+    const size_t smem = faces_smem_bytes(hcap, 256);
+    if (smem > 227 * 1024)
+      return fail(RT_ERR_INVALID, "rt_raytrace: radius too large for the batched schedule's "
+                                  "shared-memory layers; use RT_SCHED_PLAIN");
+    const int block = 256;
+    const int maxg = faces_max_grid(block, smem);
+    if (maxg <= 0) return fail(RT_ERR_CUDA, "rt_raytrace: no occupancy for the face kernel");
+    const int grid = std::max(1, std::min(n_items, maxg));
+    a.hcap = hcap;
+    a.items = items;
+    a.n_items = n_items;
+    TRY(cudaMemsetAsync(g.queue, 0, sizeof(int), g.stream));
+    TRY(launch_trace_faces(g, a, block, grid, smem));
+    g.stats.block = block;
+    g.stats.grid = grid;
+    g.stats.launches = 1;
+    g.stats.items = n_items;
+  }
+  g.stats.schedule = schedule;
+  return RT_OK;
+}
+
+}  // namespace asora
+
+using namespace asora;
+
+extern "C" {
+
+void rt_params_default(rt_params* p) {
+  if (!p) return;
+  p->sigma0_cm2 = 6.30e-18;
+  p->tau_lim = 1e-7;
+}
+
+const char* rt_last_error(void) { return g_last_error.c_str(); }
+
+long long rt_kernel_launch_count(void) { return g_launches.load(); }
+
+rt_status rt_ensemble_create(rt_grid_t* out, int nbox, const int* h_n, const double* h_cell_cm,
+                             const rt_params* p, rt_stream_t s) {
+  if (!out) return fail(RT_ERR_INVALID, "rt_ensemble_create: null handle pointer");
+  *out = nullptr;
+  if (nbox < 1 || nbox > (1 << 20) || !h_n || !h_cell_cm)
+    return fail(RT_ERR_INVALID, "rt_ensemble_create: bad box list");
+  rt_params prm;
+  rt_params_default(&prm);
+  if (p) prm = *p;
+  if (!(prm.sigma0_cm2 > 0) || !std::isfinite(prm.sigma0_cm2) || !(prm.tau_lim >= 0) ||
+      !std::isfinite(prm.tau_lim))
+    return fail(RT_ERR_INVALID, "rt_ensemble_create: bad parameters");
+  Grid* g = new Grid;
+  g->p = prm;
+  g->stream = (cudaStream_t)s;
+  g->nbox = nbox;
+  int64_t off = 0;
+  for (int b = 0; b < nbox; ++b) {
+    const int n = h_n[b];
+    const double c = h_cell_cm[b];
+    if (n < 1 || n > 4096 || !(c > 0) || !std::isfinite(c)) {
+      delete g;
+      return fail(RT_ERR_INVALID, "rt_ensemble_create: box size must be 1..4096 and cell > 0");
+    }
+    BoxDev B;
+    B.n = n;
+    B.wlo = -(n / 2);
+    B.whi = (n % 2 == 0) ? n / 2 - 1 : n / 2;
+    B.off = off;
+    B.cell = c;
+    B.inv_cell3 = 1.0 / (c * c * c);
+    B.thin_fac = prm.sigma0_cm2 / (c * c);
+    B.sig_cell = prm.sigma0_cm2 * c;
+    g->boxes_h.push_back(B);
+    off += (int64_t)n * n * n;
+    g->nmax = std::max(g->nmax, n);
+  }
+  g->ncell = off;
+  cudaError_t e = cudaSuccess;
+  e = cudaMalloc(&g->boxes_d, nbox * sizeof(BoxDev));
+  if (e == cudaSuccess) e = cudaMemcpy(g->boxes_d, g->boxes_h.data(), nbox * sizeof(BoxDev), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&g->dtau, g->ncell * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&g->dtauT, g->ncell * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&g->invn, g->ncell * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&g->queue, 16 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&g->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&g->unconv, 16 * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&g->flags, 16 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&g->counters, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(g->counters, 0, 8 * sizeof(unsigned long long));
+  for (auto& ev : g->ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&ev);
+  if (e != cudaSuccess) {
+    rt_status st = cuda_fail(e, "rt_ensemble_create");
+    free_grid(g);
+    return st;
+  }
+  *out = reinterpret_cast<rt_grid_t>(g);
+  return RT_OK;
+}
+
+rt_status rt_grid_create(rt_grid_t* out, int n, double cell_cm, const rt_params* p, rt_stream_t s) {
+  return rt_ensemble_create(out, 1, &n, &cell_cm, p, s);
+}
+
+rt_status rt_set_stream(rt_grid_t h, rt_stream_t s) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_set_stream: null grid");
+  reinterpret_cast<Grid*>(h)->stream = (cudaStream_t)s;
+  return RT_OK;
+}
+
+rt_status rt_set_tables(rt_grid_t h, int kind, int E0, int E1, int bits, const double* h_g,
+                        const double* h_h) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_set_tables: null grid");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  const int K = rt_table_nknots(E0, E1, bits);
+  if (K < 0 || E0 > 1000 || E1 > 1000 || bits > 10)
+    return fail(RT_ERR_INVALID, "rt_set_tables: need 1 <= E0,E1 <= 1000 and 0 <= bits <= 10");
+  if (kind != RT_TABLE_CHORDS && kind != RT_TABLE_GREY_EXACT)
+    return fail(RT_ERR_INVALID, "rt_set_tables: unknown table kind");
+  const int S = K - 1;
+  std::vector<double2> gc(S), hc(S);
+  if (kind == RT_TABLE_CHORDS) {
+    if (!h_g || !h_h) return fail(RT_ERR_INVALID, "rt_set_tables: knot arrays required");
+    for (int k = 0; k < K; ++k)
+      if (!std::isfinite(h_g[k]) || !std::isfinite(h_h[k]) || h_g[k] < 0 || h_h[k] < 0)
+        return fail(RT_ERR_INVALID, "rt_set_tables: knot values must be finite and >= 0");
+    auto tau = [&](int idx) {
+      if (idx == 0) return 0.0;
+      if (idx == K - 1) return std::ldexp(1.0, E1);
+      const int t = idx - 1;
+      return std::ldexp(1.0 + (double)(t & ((1 << bits) - 1)) / (double)(1 << bits), (t >> bits) - E0);
+    };
+    for (int s = 0; s < S; ++s) {
+      const double tl = tau(s), th = tau(s + 1);
+      double c1 = (h_g[s + 1] - h_g[s]) / (th - tl);
+      gc[s] = make_double2(std::fma(-c1, tl, h_g[s]), c1);
+      c1 = (h_h[s + 1] - h_h[s]) / (th - tl);
+      hc[s] = make_double2(std::fma(-c1, tl, h_h[s]), c1);
+    }
+  }
+  double2 *dg = nullptr, *dh = nullptr;
+  TRY(cudaMalloc(&dg, S * sizeof(double2)));
+  cudaError_t e = cudaMalloc(&dh, S * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMemcpy(dg, gc.data(), S * sizeof(double2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dh, hc.data(), S * sizeof(double2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(dg);
+    cudaFree(dh);
+    return cuda_fail(e, "rt_set_tables");
+  }
+  cudaFree(g.gtab);
+  cudaFree(g.htab);
+  g.gtab = dg;
+  g.htab = dh;
+  g.tab_kind = kind;
+  g.E0 = E0;
+  g.E1 = E1;
+  g.B = bits;
+  g.have_tables = true;
+  return RT_OK;
+}
+
+static rt_status set_field(rt_grid_t h, const double* d, bool density) {
+  const char* who = density ? "rt_set_density" : "rt_set_xHI";
+  if (!h) return fail(RT_ERR_INVALID, std::string(who) + ": null grid");
+  if (!d) return fail(RT_ERR_INVALID, std::string(who) + ": null field");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  int herr = 0;
+  TRY(cudaMemsetAsync(g.err, 0, sizeof(int), g.stream));
+  TRY(launch_validate_fields(g, density ? d : nullptr, density ? nullptr : d));
+  TRY(cudaMemcpyAsync(&herr, g.err, sizeof(int), cudaMemcpyDeviceToHost, g.stream));
+  TRY(cudaStreamSynchronize(g.stream));
+  if (herr)
+    return fail(RT_ERR_INVALID, density ? "rt_set_density: n_H must be finite, >= +0 and <= 1e12"
+                                        : "rt_set_xHI: x_HI must lie in [+0, 1]");
+  if (density) g.nH = d; else g.xHI = d;
+  return RT_OK;
+}
+
+rt_status rt_set_density(rt_grid_t h, const double* d_nH) { return set_field(h, d_nH, true); }
+rt_status rt_set_xHI(rt_grid_t h, const double* d_xHI) { return set_field(h, d_xHI, false); }
+
+rt_status rt_set_sources(rt_grid_t h, int nsrc, const int32_t* d_pos, const int32_t* d_box,
+                         const double* d_ndot, const double* d_radius) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_set_sources: null grid");
+  if (nsrc < 0 || nsrc > (1 << 27)) return fail(RT_ERR_INVALID, "rt_set_sources: bad source count");
+  if (nsrc > 0 && (!d_pos || !d_ndot || !d_radius))
+    return fail(RT_ERR_INVALID, "rt_set_sources: null source array");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  rt_status st = ingest_sources(g, nsrc, d_pos, d_box, d_ndot, d_radius);
+  if (st != RT_OK) return st;
+  const int mmax = std::max(1, std::min(isqrt_h(g.max_r2), g.nmax / 2 + 1));
+  return ensure_geometry(g, mmax);
+}
+
+rt_status rt_raytrace(rt_grid_t h, double* d_gamma, int schedule) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_raytrace: null grid");
+  if (!d_gamma) return fail(RT_ERR_INVALID, "rt_raytrace: null output");
+  if (schedule != RT_SCHED_AUTO && schedule != RT_SCHED_PLAIN && schedule != RT_SCHED_BATCHED)
+    return fail(RT_ERR_INVALID, "rt_raytrace: unknown schedule");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  rt_status st = check_ready(g, "rt_raytrace");
+  if (st != RT_OK) return st;
+  TRY(cudaEventRecord(g.ev[0], g.stream));
+  TRY(launch_precompute(g));
+  TRY(cudaMemsetAsync(d_gamma, 0, g.ncell * sizeof(double), g.stream));
+  TRY(cudaEventRecord(g.ev[1], g.stream));
+  if (g.nsrc > 0) {
+    if (schedule == RT_SCHED_PLAIN)
+      st = run_trace(g, d_gamma, nullptr, nullptr, g.nsrc, RT_SCHED_PLAIN, g.nsrc);
+    else
+      st = run_trace(g, d_gamma, nullptr, g.items, 6 * g.nsrc, RT_SCHED_BATCHED, g.nsrc);
+    if (st != RT_OK) return st;
+  } else {
+    g.stats.launches = 0;
+    g.stats.items = 0;
+  }
+  TRY(cudaEventRecord(g.ev[2], g.stream));
+  g.stats.source_voxels = g.source_voxels;
+  return RT_OK;
+}
+
+rt_status rt_raytrace_source_coldens(rt_grid_t h, int src, double* d_coldens, int schedule) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_raytrace_source_coldens: null grid");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  if (!d_coldens) return fail(RT_ERR_INVALID, "rt_raytrace_source_coldens: null output");
+  if (src < 0 || src >= g.nsrc_in)
+    return fail(RT_ERR_INVALID, "rt_raytrace_source_coldens: source index out of range");
+  rt_status st = check_ready(g, "rt_raytrace_source_coldens");
+  if (st != RT_OK) return st;
+  int p = 0;
+  TRY(cudaMemcpyAsync(&p, g.src_of_input + src, sizeof(int), cudaMemcpyDeviceToHost, g.stream));
+  TRY(cudaStreamSynchronize(g.stream));
+  int hitems[6];
+  for (int f = 0; f < 6; ++f) hitems[f] = (p << 3) | f;
+  TRY(cudaMemcpyAsync(g.queue + 8, hitems, 6 * sizeof(int), cudaMemcpyHostToDevice, g.stream));
+  TRY(launch_precompute(g));
+  TRY(cudaMemsetAsync(d_coldens, 0, g.ncell * sizeof(double), g.stream));
+  if (schedule == RT_SCHED_PLAIN) {
+    hitems[0] = p;
+    TRY(cudaMemcpyAsync(g.queue + 8, hitems, sizeof(int), cudaMemcpyHostToDevice, g.stream));
+    st = run_trace(g, nullptr, d_coldens, g.queue + 8, 1, RT_SCHED_PLAIN, 1);
+  } else {
+    st = run_trace(g, nullptr, d_coldens, g.queue + 8, 6, RT_SCHED_BATCHED, 0);
+  }
+  if (st != RT_OK) return st;
+  TRY(cudaStreamSynchronize(g.stream));  // hitems is a stack buffer
+  return RT_OK;
+}
+
+rt_status rt_get_stats(rt_grid_t h, rt_stats* out) {
+  if (!h || !out) return fail(RT_ERR_INVALID, "rt_get_stats: null argument");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  TRY(cudaStreamSynchronize(g.stream));
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, g.ev[1], g.ev[2]) == cudaSuccess) g.stats.trace_ms = ms;
+  if (cudaEventElapsedTime(&ms, g.ev[0], g.ev[1]) == cudaSuccess) g.stats.prep_ms = ms;
+  cudaGetLastError();
+  unsigned long long rc = 0;
+  TRY(cudaMemcpy(&rc, g.counters, sizeof(rc), cudaMemcpyDeviceToHost));
+  g.stats.rate_cells = (int64_t)rc;
+  g.stats.kernel_launches = g_launches.load();
+  *out = g.stats;
+  int herr = 0;
+  TRY(cudaMemcpy(&herr, g.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) {
+    cudaMemset(g.err, 0, sizeof(int));
+    return fail(RT_ERR_CUDA, "device-side bounds check failed (error bits " + std::to_string(herr) + ")");
+  }
+  return RT_OK;
+}
+
+rt_status rt_chemistry_step(rt_grid_t h, const double* d_gamma, const double* d_x0,
+                            const double* d_xavg_in, double dt_s, double alpha_H, double C_H,
+                            double conv_tol, double* d_xavg_out, double* d_xnew_out,
+                            int64_t* d_unconverged) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_chemistry_step: null grid");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  if (!d_gamma || !d_x0 || !d_xavg_in || !d_xavg_out || !d_xnew_out || !d_unconverged)
+    return fail(RT_ERR_INVALID, "rt_chemistry_step: null pointer");
+  if (!(dt_s > 0) || !std::isfinite(dt_s) || !(alpha_H >= 0) || !(C_H >= 0) || !(conv_tol >= 0))
+    return fail(RT_ERR_INVALID, "rt_chemistry_step: need dt > 0, alpha_H >= 0, C_H >= 0");
+  if (!g.nH) return fail(RT_ERR_STATE, "rt_chemistry_step: rt_set_density not called");
+  TRY(launch_chemistry(g, d_gamma, d_x0, d_xavg_in, dt_s, alpha_H, C_H, 1e-10, 50, conv_tol,
+                       d_xavg_out, d_xnew_out, d_unconverged, nullptr));
+  return RT_OK;
+}
+
+rt_status rt_iterate(rt_grid_t h, double* d_x, double dt_s, double alpha_H, double C_H,
+                     int max_iter, double conv_tol, double conv_frac, int use_graph,
+                     double* d_gamma, int* h_iters) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_iterate: null grid");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  if (!d_x || !d_gamma) return fail(RT_ERR_INVALID, "rt_iterate: null pointer");
+  if (max_iter < 1 || max_iter > 1000 || !(dt_s > 0) || !(alpha_H >= 0) || !(C_H >= 0) ||
+      !(conv_tol >= 0) || !(conv_frac >= 0))
+    return fail(RT_ERR_INVALID, "rt_iterate: bad arguments");
+  if (!g.have_tables) return fail(RT_ERR_STATE, "rt_iterate: rt_set_tables not called");
+  if (!g.nH) return fail(RT_ERR_STATE, "rt_iterate: rt_set_density not called");
+  const size_t bytes = g.ncell * sizeof(double);
+  if (!g.xbuf) {
+    TRY(cudaMalloc(&g.xbuf, bytes));
+    TRY(cudaMalloc(&g.xavg, bytes));
+    TRY(cudaMalloc(&g.xavg2, bytes));
+    TRY(cudaMalloc(&g.xhi_int, bytes));
+  }
+  g.xHI = g.xhi_int;
+  const int64_t limit = (int64_t)std::ceil(conv_frac * (double)g.ncell);
+  cudaStream_t user = g.stream;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  rt_status st = RT_OK;
+  int iters = 0;
+  auto body = [&](int k) -> rt_status {
+    const int* skip = g.flags;
+    double* xin = (k % 2 == 0) ? g.xavg : g.xavg2;
+    double* xout = (k % 2 == 0) ? g.xavg2 : g.xavg;
+    TRY(launch_one_minus(xin, g.xhi_int, g.ncell, skip, g.stream));
+    TRY(launch_precompute(g, skip));
+    TRY(launch_zero(d_gamma, g.ncell, skip, g.stream));
+    TRY(cudaMemsetAsync(g.unconv, 0, sizeof(int64_t), g.stream));
+    if (g.nsrc > 0) {
+      rt_status s2 = run_trace(g, d_gamma, nullptr, g.items, 6 * g.nsrc, RT_SCHED_BATCHED, g.nsrc, skip);
+      if (s2 != RT_OK) return s2;
+    }
+    TRY(launch_chemistry(g, d_gamma, d_x, xin, dt_s, alpha_H, C_H, 1e-10, 50, conv_tol, xout,
+                         g.xbuf, g.unconv, skip));
+    TRY(launch_conv_check(g.unconv, limit, g.flags, g.stream));
+    return RT_OK;
+  };
+  TRY(cudaMemcpyAsync(g.xavg, d_x, bytes, cudaMemcpyDeviceToDevice, user));
+  TRY(cudaMemsetAsync(g.flags, 0, 2 * sizeof(int), user));
+  if (use_graph) {
+    // capture on a private stream ordered after the user's stream
+    TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    TRY(cudaEventRecord(g.ev[3], user));
+    TRY(cudaStreamWaitEvent(cap, g.ev[3], 0));
+    g.stream = cap;
+    g.capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      for (int k = 0; k < max_iter && st == RT_OK; ++k) st = body(k);
+      cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+      if (st == RT_OK && e2 != cudaSuccess) st = cuda_fail(e2, "cudaStreamEndCapture");
+    } else {
+      st = cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    g.capturing = false;
+    g.stream = user;
+    if (st == RT_OK) {
+      cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+      if (e3 == cudaSuccess) e3 = cudaGraphLaunch(exec, cap);
+      if (e3 == cudaSuccess) e3 = cudaEventRecord(g.ev[3], cap);
+      if (e3 == cudaSuccess) e3 = cudaStreamWaitEvent(user, g.ev[3], 0);
+      if (e3 != cudaSuccess) st = cuda_fail(e3, "graph launch");
+    }
+    if (exec) cudaGraphExecDestroy(exec);  // deferred until the launch completes
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    if (st != RT_OK) return st;
+  } else {
+    for (int k = 0; k < max_iter; ++k) {
+      st = body(k);
+      if (st != RT_OK) return st;
+      int fl[2] = {0, 0};
+      TRY(cudaMemcpyAsync(fl, g.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, user));
+      TRY(cudaStreamSynchronize(user));
+      if (fl[0]) break;
+    }
+  }
+  TRY(cudaMemcpyAsync(d_x, g.xbuf, bytes, cudaMemcpyDeviceToDevice, user));
+  if (h_iters) {
+    int fl[2] = {0, 0};
+    TRY(cudaMemcpyAsync(fl, g.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, user));
+    TRY(cudaStreamSynchronize(user));
+    iters = fl[1];
+    *h_iters = iters;
+  }
+  return RT_OK;
+}
+
+void rt_grid_destroy(rt_grid_t h) {
+  if (!h) return;
+  Grid* g = reinterpret_cast<Grid*>(h);
+  cudaStreamSynchronize(g->stream);
+  free_grid(g);
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// Internal declarations shared by the CUDA translation units of libasora.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/asora.h"
+
+namespace asora {
+
+// ------------------------------------------------------------------ boxes
+struct BoxDev {
+  int n;            // cells per side
+  int wlo, whi;     // periodic window of offsets: [-n/2, n/2-1] (even), [-(n-1)/2,(n-1)/2] (odd)
+  int64_t off;      // first cell of this box in the concatenated fields
+  double cell;      // cell size (cm)
+  double inv_cell3; // 1/cell^3
+  double thin_fac;  // sigma0 / cell^2
+  double sig_cell;  // sigma0 * cell
+};
+
+// Source after ingest (merged, LPT ordered).
+struct SrcDev {
+  int i, j, k, box;
+};
+
+// Geometry of one canonical offset (m = |Delta_d| dominant, lo <= hi the two
+// transverse magnitudes), source- and box-independent:
+//   x = lo/m, y = hi/m,  W1 = (1-x)(1-y), WA = x(1-y), WB = (1-x)y, W4 = xy,
+//   ds = sqrt(1 + (lo^2+hi^2)/m^2), invV = 1/(4 pi r2 ds), thin = 1/(4 pi r2),
+//   r2 = m^2 + lo^2 + hi^2 (cells^2).
+struct __align__(16) GeoEntry {
+  double w1, wa, wb, w4;
+  double ds, invv, thin, pad;
+};
+// Index of (m, lo, hi), 1 <= m, 0 <= lo <= hi <= m.
+__host__ __device__ inline int64_t geo_index(int m, int lo, int hi) {
+  return (int64_t)(m + 2) * (m + 1) * m / 6 - 1 + (int64_t)hi * (hi + 1) / 2 + lo;
+}
+inline int64_t geo_count(int mmax) { return geo_index(mmax + 1, 0, 0); }
+
+// Rate tables on the device.
+struct TabDev {
+  const double2* g;  // (c0, c1) per segment
+  const double2* h;
+  int kind;          // RT_TABLE_*
+  int E0, B;
+  uint64_t tau_min_bits, tau_max_bits;  // bits of 2^-E0 and of the "no transmission" bound
+};
+
+// Arguments of the trace kernels.
+struct TraceArgs {
+  const BoxDev* boxes;
+  const double* dtau;    // sigma0*cell*n_H*x_HI, C order per box
+  const double* dtauT;   // the same, axes rotated to (k, i, j) per box
+  const double* invn;    // 1/(n_H x_HI)
+  double* gamma;         // output rates (may be null)
+  double* coldens;       // optional per-source column density output
+  const SrcDev* src;
+  const double* ndot;
+  const int* r2lim;      // floor(R^2) per source
+  const int* items;      // (source << 3) | face, LPT order
+  int n_items;
+  int* queue;            // work counter
+  const GeoEntry* geo;
+  int geo_mmax;
+  TabDev tab;
+  double tau_lim;
+  double sigma0;
+  int hcap;              // layer half-size capacity (faces) / cube half-size (shells)
+  double* scratch;       // per-CTA scratch (shell kernel)
+  int* err;              // error flag (bit mask)
+  const int* skip;       // if non-null and *skip != 0 the launch does nothing
+  unsigned long long* rate_cells;  // number of rate evaluations (may be null)
+};
+
+enum ErrBits { ERR_LAYER_CAP = 1, ERR_GEO = 2, ERR_INPUT = 4, ERR_CUBE = 8 };
+
+// ----------------------------------------------------------- grid (handle)
+struct Grid {
+  int nbox = 0;
+  std::vector<BoxDev> boxes_h;
+  BoxDev* boxes_d = nullptr;
+  int64_t ncell = 0;
+  int nmax = 0;
+  rt_params p{};
+  cudaStream_t stream = nullptr;
+
+  // tables
+  bool have_tables = false;
+  int tab_kind = 0, E0 = 0, E1 = 0, B = 0;
+  double2* gtab = nullptr;
+  double2* htab = nullptr;
+
+  // inputs (borrowed)
+  const double* nH = nullptr;
+  const double* xHI = nullptr;
+  bool dirty_fields = true;
+
+  // derived per-cell fields (owned)
+  double* dtau = nullptr;
+  double* dtauT = nullptr;
+  double* invn = nullptr;
+
+  // sources (owned, ingested)
+  int nsrc_in = 0;         // as given
+  int nsrc = 0;            // after merging
+  SrcDev* src = nullptr;
+  double* ndot = nullptr;
+  int* r2lim = nullptr;
+  int* items = nullptr;    // 6 per source, LPT order
+  int* src_of_input = nullptr;  // merged index of each input source
+  int max_r2 = 0;
+  int64_t source_voxels = 0;
+  std::vector<int> r2_sorted_h;  // per merged source (LPT order), host copy
+
+  // geometry
+  GeoEntry* geo = nullptr;
+  int geo_mmax = 0;
+
+  // scratch
+  int* queue = nullptr;
+  int* err = nullptr;
+  double* cube = nullptr;       // shell-kernel scratch
+  size_t cube_bytes = 0;
+  int64_t* unconv = nullptr;    // iteration counters
+  double* xbuf = nullptr;       // rt_iterate buffers
+  double* xavg = nullptr;
+  double* xavg2 = nullptr;
+  double* xhi_int = nullptr;
+  int* flags = nullptr;
+  unsigned long long* counters = nullptr;  // [0]: rate evaluations of the last trace
+  bool capturing = false;
+
+  // stats
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  rt_stats stats{};
+};
+
+// Kernels launched by this library in this process (host-side count).
+void count_launch(int n = 1);
+
+// error reporting (api.cu)
+rt_status fail(rt_status st, const std::string& msg);
+rt_status cuda_fail(cudaError_t e, const char* what);
+
+// launchers (defined in the kernel translation units)
+cudaError_t launch_precompute(Grid& g, const int* skip = nullptr);
+cudaError_t launch_zero(double* p, int64_t n, const int* skip, cudaStream_t s);
+cudaError_t launch_validate_fields(Grid& g, const double* nH, const double* xHI);
+cudaError_t launch_geometry(GeoEntry* geo, int mmax, cudaStream_t s);
+cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid, size_t smem);
+cudaError_t launch_trace_shells(Grid& g, const TraceArgs& a, int block, int grid);
+size_t faces_smem_bytes(int hcap, int block);
+int faces_max_grid(int block, size_t smem);
+int shells_max_grid(int block);
+rt_status ingest_sources(Grid& g, int nsrc, const int32_t* d_pos, const int32_t* d_box,
+                         const double* d_ndot, const double* d_radius);
+cudaError_t launch_chemistry(Grid& g, const double* gamma, const double* x0, const double* xavg_in,
+                             double dt, double alpha_H, double C_H, double tol, int maxit,
+                             double conv_tol, double* xavg_out, double* xnew_out,
+                             int64_t* unconv, const int* skip_flag);
+cudaError_t launch_one_minus(const double* x, double* y, int64_t n, const int* skip_flag,
+                             cudaStream_t s);
+cudaError_t launch_conv_check(const int64_t* unconv, int64_t limit, int* flag, cudaStream_t s);
+
+}  // namespace asora

@@ -1,0 +1,370 @@
+// Per-call preparation kernels: field validation, per-cell optical depth
+// (Sec. 3.1: dtau = sigma0 * alpha * n_HI), its axis-rotated copy for the
+// z faces, 1/n_HI, the source-independent geometry table and source ingest
+// (merging of co-located sources, Sec. 3, and longest-first ordering).
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "asora_internal.cuh"
+
+namespace asora {
+
+// ----------------------------------------------------------- validation
+__global__ void k_validate_fields(const BoxDev* __restrict__ boxes, int nbox,
+                                  const double* __restrict__ nH, const double* __restrict__ xHI,
+                                  int64_t ncell, int* __restrict__ err) {
+  int bad = 0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    if (nH) {
+      const double v = nH[c];
+      if (!(v >= 0.0) || !isfinite(v) || signbit(v) || v > 1e12) bad = 1;
+    }
+    if (xHI) {
+      const double v = xHI[c];
+      if (!(v >= 0.0) || !(v <= 1.0) || signbit(v)) bad = 1;
+    }
+  }
+  if (bad) atomicOr(err, ERR_INPUT);
+}
+
+cudaError_t launch_validate_fields(Grid& g, const double* nH, const double* xHI) {
+  k_validate_fields<<<1024, 256, 0, g.stream>>>(g.boxes_d, g.nbox, nH, xHI, g.ncell, g.err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------- per-cell fields
+// One 32x32 tile of the (n^2 rows (i,j)) x (n cols k) matrix of a box:
+// dtau = ((sigma0*cell)*n_H)*x_HI, invn = 1/(n_H*x_HI), and the transposed
+// copy dtauT[k][i][j] so that the z faces read rows of constant k contiguously.
+__global__ void k_precompute(const BoxDev* __restrict__ boxes, const double* __restrict__ nH,
+                             const double* __restrict__ xHI, double* __restrict__ dtau,
+                             double* __restrict__ dtauT, double* __restrict__ invn,
+                             const int* __restrict__ skip) {
+  __shared__ double tile[32][33];
+  if (skip && *skip) return;
+  const BoxDev B = boxes[blockIdx.z];
+  const int n = B.n;
+  const int64_t rows = (int64_t)n * n;
+  const int c0 = blockIdx.x * 32;
+  if (c0 >= n) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int64_t r0 = (int64_t)blockIdx.y * 32; r0 < rows; r0 += (int64_t)gridDim.y * 32) {
+    for (int yy = ty; yy < 32; yy += 8) {
+      const int64_t r = r0 + yy;
+      const int c = c0 + tx;
+      if (r < rows && c < n) {
+        const int64_t idx = B.off + r * n + c;
+        const double nh = nH[idx], x = xHI[idx];
+        const double d = (B.sig_cell * nh) * x;
+        dtau[idx] = d;
+        invn[idx] = 1.0 / (nh * x);
+        tile[yy][tx] = d;
+      }
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+      const int c = c0 + yy;        // k
+      const int64_t r = r0 + tx;    // (i,j)
+      if (r < rows && c < n) dtauT[B.off + (int64_t)c * rows + r] = tile[tx][yy];
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_precompute(Grid& g, const int* skip) {
+  const int n = g.nmax;
+  dim3 grid((n + 31) / 32, (unsigned)std::min<int64_t>(((int64_t)n * n + 31) / 32, 65535), g.nbox);
+  k_precompute<<<grid, dim3(32, 8), 0, g.stream>>>(g.boxes_d, g.nH, g.xHI, g.dtau, g.dtauT,
+                                                    g.invn, skip);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_zero(double* __restrict__ p, int64_t n, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x)
+    p[c] = 0.0;
+}
+
+cudaError_t launch_zero(double* p, int64_t n, const int* skip, cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  k_zero<<<grid, 256, 0, s>>>(p, n, skip);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- geometry
+// Entry (m, lo, hi): bilinear weights of Sec. 3.1 for a = lo/m, b = hi/m and
+// the path length ds = sqrt(1 + (lo^2+hi^2)/m^2).  Both are computed with
+// correctly rounded IEEE division and square root.
+__global__ void k_geometry(GeoEntry* __restrict__ geo, int mmax) {
+  const int m = blockIdx.x + 1;
+  if (m > mmax) return;
+  const int cnt = (m + 1) * (m + 2) / 2;
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    int hi = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while (hi * (hi + 1) / 2 > t) --hi;
+    while ((hi + 1) * (hi + 2) / 2 <= t) ++hi;
+    const int lo = t - hi * (hi + 1) / 2;
+    const double x = (double)lo / (double)m;
+    const double y = (double)hi / (double)m;
+    GeoEntry e;
+    e.w1 = (1.0 - x) * (1.0 - y);
+    e.wa = x * (1.0 - y);
+    e.wb = (1.0 - x) * y;
+    e.w4 = x * y;
+    e.ds = sqrt(1.0 + (double)(lo * lo + hi * hi) / (double)(m * m));
+    const double r2 = (double)(m * m + lo * lo + hi * hi);
+    const double fourpi = 12.566370614359172;
+    e.invv = 1.0 / (fourpi * r2 * e.ds);
+    e.thin = 1.0 / (fourpi * r2);
+    e.pad = 0.0;
+    geo[geo_index(m, lo, hi)] = e;
+  }
+}
+
+cudaError_t launch_geometry(GeoEntry* geo, int mmax, cudaStream_t s) {
+  if (mmax < 1) return cudaSuccess;
+  k_geometry<<<mmax, 256, 0, s>>>(geo, mmax);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------- source ingest
+__global__ void k_src_keys(const BoxDev* __restrict__ boxes, int nbox, int nsrc,
+                           const int32_t* __restrict__ pos, const int32_t* __restrict__ box,
+                           const double* __restrict__ ndot, const double* __restrict__ radius,
+                           uint64_t* __restrict__ keys, int* __restrict__ idx,
+                           int* __restrict__ r2out, int* __restrict__ err) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsrc) return;
+  const int b = box ? box[s] : 0;
+  bool bad = b < 0 || b >= nbox;
+  const BoxDev B = boxes[bad ? 0 : b];
+  const int i = pos[3 * s], j = pos[3 * s + 1], k = pos[3 * s + 2];
+  bad |= i < 0 || i >= B.n || j < 0 || j >= B.n || k < 0 || k >= B.n;
+  const double R = radius[s], nd = ndot[s];
+  bad |= !(R > 0.0) || !isfinite(R) || !(nd >= 0.0) || !isfinite(nd) || signbit(nd);
+  // traced cells satisfy |Delta|^2 <= floor(R^2); every window cell has
+  // |Delta|^2 <= 3 (n/2)^2, so larger limits trace the same set.
+  const double cap = 3.0 * (double)(B.n / 2) * (double)(B.n / 2) + 1.0;
+  const double rr = fmin(floor(R * R), cap);
+  const int r2 = bad ? 0 : (int)rr;
+  if (bad) atomicOr(err, ERR_INPUT);
+  const int64_t cell = bad ? 0 : B.off + ((int64_t)i * B.n + j) * B.n + k;
+  keys[s] = ((uint64_t)cell << 22) | (uint64_t)r2;
+  idx[s] = s;
+  r2out[s] = r2;
+}
+
+__global__ void k_src_heads(const uint64_t* __restrict__ keys, int nsrc, int* __restrict__ head) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nsrc) return;
+  head[t] = (t == 0 || keys[t] != keys[t - 1]) ? 1 : 0;
+}
+
+// Merged source m = segment starting at sorted position t: rates summed in
+// input order; LPT sort key = (max_r2 - r2) ascending.
+__global__ void k_src_merge(const uint64_t* __restrict__ keys, const int* __restrict__ idx,
+                            const int* __restrict__ head, const int* __restrict__ mid, int nsrc,
+                            const int32_t* __restrict__ pos, const int32_t* __restrict__ box,
+                            const double* __restrict__ ndot, const int* __restrict__ r2in,
+                            SrcDev* __restrict__ msrc, double* __restrict__ mndot,
+                            int* __restrict__ mr2, uint32_t* __restrict__ lkey,
+                            int* __restrict__ lval, int* __restrict__ src_of_input, int max_r2) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nsrc) return;
+  // mid = exclusive scan of head flags: a segment head's own index; any other
+  // member sees its head counted already.
+  const int m = mid[t] + head[t] - 1;
+  src_of_input[idx[t]] = m;  // merged index, remapped to LPT order later
+  if (!head[t]) return;
+  const int s0 = idx[t];
+  double sum = 0.0;
+  for (int u = t; u < nsrc && (u == t || !head[u]); ++u) sum += ndot[idx[u]];
+  SrcDev d;
+  d.i = pos[3 * s0];
+  d.j = pos[3 * s0 + 1];
+  d.k = pos[3 * s0 + 2];
+  d.box = box ? box[s0] : 0;
+  msrc[m] = d;
+  mndot[m] = sum;
+  mr2[m] = r2in[s0];
+  lkey[m] = (uint32_t)(max_r2 - r2in[s0]);
+  lval[m] = m;
+}
+
+// Permute merged sources into LPT order and emit 6 face items per source.
+__global__ void k_src_order(const int* __restrict__ order, int nm, const SrcDev* __restrict__ msrc,
+                            const double* __restrict__ mndot, const int* __restrict__ mr2,
+                            SrcDev* __restrict__ src, double* __restrict__ ndot,
+                            int* __restrict__ r2lim, int* __restrict__ items,
+                            int* __restrict__ lpt_of_merged) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nm) return;
+  const int m = order[p];
+  src[p] = msrc[m];
+  ndot[p] = mndot[m];
+  r2lim[p] = mr2[m];
+  lpt_of_merged[m] = p;
+  for (int f = 0; f < 6; ++f) items[6 * p + f] = (p << 3) | f;
+}
+
+__global__ void k_remap(int* __restrict__ a, const int* __restrict__ map, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) a[t] = map[a[t]];
+}
+
+static int64_t ball_count(int r2, int n) {
+  const int wlo = -(n / 2), whi = (n % 2 == 0) ? n / 2 - 1 : n / 2;
+  int64_t cnt = 0;
+  const int L = std::min((int)std::floor(std::sqrt((double)r2)) + 1, n);
+  for (int a = std::max(-L, wlo); a <= std::min(L, whi); ++a)
+    for (int b = std::max(-L, wlo); b <= std::min(L, whi); ++b) {
+      const int64_t rem = (int64_t)r2 - (int64_t)a * a - (int64_t)b * b;
+      if (rem < 0) continue;
+      int w = (int)std::floor(std::sqrt((double)rem));
+      while ((int64_t)w * w > rem) --w;
+      while ((int64_t)(w + 1) * (w + 1) <= rem) ++w;
+      cnt += std::min(w, whi) - std::max(-w, wlo) + 1;
+    }
+  return cnt;
+}
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) {                    \
+      st = cuda_fail(e_, #x);                   \
+      goto done;                                \
+    }                                           \
+  } while (0)
+
+rt_status ingest_sources(Grid& g, int nsrc, const int32_t* d_pos, const int32_t* d_box,
+                         const double* d_ndot, const double* d_radius) {
+  rt_status st = RT_OK;
+  cudaStream_t s = g.stream;
+  uint64_t *keys = nullptr, *keys2 = nullptr;
+  int *idx = nullptr, *idx2 = nullptr, *r2in = nullptr, *head = nullptr, *mid = nullptr;
+  SrcDev* msrc = nullptr;
+  double* mndot = nullptr;
+  int* mr2 = nullptr;
+  uint32_t *lkey = nullptr, *lkey2 = nullptr;
+  int *lval = nullptr, *order = nullptr, *lpt_of_merged = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_bytes = 0, need = 0;
+  int nm = 0, last_head = 0, last_mid = 0;
+  int herr = 0;
+  const int T = 256;
+  const int nb = (nsrc + T - 1) / T;
+
+  // free previous sources
+  cudaFree(g.src); cudaFree(g.ndot); cudaFree(g.r2lim); cudaFree(g.items); cudaFree(g.src_of_input);
+  g.src = nullptr; g.ndot = nullptr; g.r2lim = nullptr; g.items = nullptr; g.src_of_input = nullptr;
+  g.nsrc = 0; g.nsrc_in = 0; g.max_r2 = 0; g.source_voxels = 0; g.r2_sorted_h.clear();
+  if (nsrc == 0) return RT_OK;
+
+  CK(cudaMalloc(&keys, nsrc * sizeof(uint64_t)));
+  CK(cudaMalloc(&keys2, nsrc * sizeof(uint64_t)));
+  CK(cudaMalloc(&idx, nsrc * sizeof(int)));
+  CK(cudaMalloc(&idx2, nsrc * sizeof(int)));
+  CK(cudaMalloc(&r2in, nsrc * sizeof(int)));
+  CK(cudaMalloc(&head, nsrc * sizeof(int)));
+  CK(cudaMalloc(&mid, nsrc * sizeof(int)));
+  CK(cudaMemsetAsync(g.err, 0, sizeof(int), s));
+  k_src_keys<<<nb, T, 0, s>>>(g.boxes_d, g.nbox, nsrc, d_pos, d_box, d_ndot, d_radius, keys, idx,
+                              r2in, g.err);
+  count_launch();
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&herr, g.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (herr) {
+    st = fail(RT_ERR_INVALID, "rt_set_sources: source outside its box, bad box id, radius <= 0 "
+                              "or non-finite/negative photon rate");
+    goto done;
+  }
+  // stable sort by (cell, r2): co-located sources with equal radius become adjacent
+  CK(cub::DeviceRadixSort::SortPairs(nullptr, need, keys, keys2, idx, idx2, nsrc, 0, 64, s));
+  tmp_bytes = need;
+  CK(cub::DeviceScan::ExclusiveSum(nullptr, need, head, mid, nsrc, s));
+  tmp_bytes = std::max(tmp_bytes, need);
+  CK(cub::DeviceRadixSort::SortPairs(nullptr, need, lkey, lkey2, lval, order, nsrc, 0, 32, s));
+  tmp_bytes = std::max(tmp_bytes, need);
+  CK(cudaMalloc(&tmp, tmp_bytes));
+  need = tmp_bytes;
+  CK(cub::DeviceRadixSort::SortPairs(tmp, need, keys, keys2, idx, idx2, nsrc, 0, 64, s));
+  k_src_heads<<<nb, T, 0, s>>>(keys2, nsrc, head);
+  count_launch();
+  CK(cudaGetLastError());
+  need = tmp_bytes;
+  CK(cub::DeviceScan::ExclusiveSum(tmp, need, head, mid, nsrc, s));
+  CK(cudaMemcpyAsync(&last_head, head + nsrc - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&last_mid, mid + nsrc - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  nm = last_mid + last_head;
+  {
+    // max r2 for the LPT key
+    std::vector<int> r2h(nsrc);
+    CK(cudaMemcpy(r2h.data(), r2in, nsrc * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int v : r2h) g.max_r2 = std::max(g.max_r2, v);
+  }
+  CK(cudaMalloc(&msrc, nm * sizeof(SrcDev)));
+  CK(cudaMalloc(&mndot, nm * sizeof(double)));
+  CK(cudaMalloc(&mr2, nm * sizeof(int)));
+  CK(cudaMalloc(&lkey, nm * sizeof(uint32_t)));
+  CK(cudaMalloc(&lkey2, nm * sizeof(uint32_t)));
+  CK(cudaMalloc(&lval, nm * sizeof(int)));
+  CK(cudaMalloc(&order, nm * sizeof(int)));
+  CK(cudaMalloc(&lpt_of_merged, nm * sizeof(int)));
+  CK(cudaMalloc(&g.src_of_input, nsrc * sizeof(int)));
+  k_src_merge<<<nb, T, 0, s>>>(keys2, idx2, head, mid, nsrc, d_pos, d_box, d_ndot, r2in, msrc,
+                               mndot, mr2, lkey, lval, g.src_of_input, g.max_r2);
+  count_launch();
+  CK(cudaGetLastError());
+  need = tmp_bytes;
+  CK(cub::DeviceRadixSort::SortPairs(tmp, need, lkey, lkey2, lval, order, nm, 0, 32, s));
+  CK(cudaMalloc(&g.src, nm * sizeof(SrcDev)));
+  CK(cudaMalloc(&g.ndot, nm * sizeof(double)));
+  CK(cudaMalloc(&g.r2lim, nm * sizeof(int)));
+  CK(cudaMalloc(&g.items, (size_t)6 * nm * sizeof(int)));
+  k_src_order<<<(nm + T - 1) / T, T, 0, s>>>(order, nm, msrc, mndot, mr2, g.src, g.ndot, g.r2lim,
+                                             g.items, lpt_of_merged);
+  count_launch();
+  CK(cudaGetLastError());
+  k_remap<<<nb, T, 0, s>>>(g.src_of_input, lpt_of_merged, nsrc);
+  count_launch();
+  CK(cudaGetLastError());
+  {
+    g.r2_sorted_h.resize(nm);
+    std::vector<SrcDev> sh(nm);
+    CK(cudaMemcpyAsync(g.r2_sorted_h.data(), g.r2lim, nm * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(sh.data(), g.src, nm * sizeof(SrcDev), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::map<std::pair<int, int>, int64_t> memo;
+    int64_t sv = 0;
+    for (int p = 0; p < nm; ++p) {
+      const int n = g.boxes_h[sh[p].box].n;
+      auto key = std::make_pair(g.r2_sorted_h[p], n);
+      auto it = memo.find(key);
+      if (it == memo.end()) it = memo.emplace(key, ball_count(key.first, n)).first;
+      sv += it->second;
+    }
+    g.source_voxels = sv;
+  }
+  g.nsrc = nm;
+  g.nsrc_in = nsrc;
+done:
+  cudaFree(keys); cudaFree(keys2); cudaFree(idx); cudaFree(idx2); cudaFree(r2in);
+  cudaFree(head); cudaFree(mid); cudaFree(msrc); cudaFree(mndot); cudaFree(mr2);
+  cudaFree(lkey); cudaFree(lkey2); cudaFree(lval); cudaFree(order); cudaFree(lpt_of_merged);
+  cudaFree(tmp);
+  return st;
+}
+
+}  // namespace asora

@@ -1,0 +1,258 @@
+"""GPU <-> oracle parity through the C ABI (libasora via the ctypes binding).
+
+Bar: column densities bit-identical (same operations, same roundings),
+Gamma within 1e-9 relative (only the order of the atomic sums over sources
+differs), identical zero patterns.  Rate tables are inputs of the ray trace
+(Eq. tables, pre-tabulated): both sides receive the same knot values, taken
+from the oracle's own quadrature.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2311_01492_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+GAMMA_RTOL = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2311_01492_gb300 import build
+    build.build()
+
+
+def A():
+    from paper_2311_01492_gb300 import api
+    return api
+
+
+_TABLES = {}
+
+
+def table(spec):
+    if spec not in _TABLES:
+        _TABLES[spec] = O.make_table(spec)
+    return _TABLES[spec]
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda").to(dtype).contiguous()
+
+
+def make_gpu(n, cell, nH, xHI, pos, ndot, R, tab, box=None, sizes=None):
+    api = A()
+    g = api.Grid(n, cell) if sizes is None else api.Grid.ensemble(sizes, cell)
+    if tab.kind == 1:
+        g.set_tables("grey_exact")
+    else:
+        g.set_tables("knots", g=tab.g, h=tab.h)
+    g.set_density(dev(nH.reshape(-1)))
+    g.set_xHI(dev(xHI.reshape(-1)))
+    g.set_sources(dev(pos, torch.int32), dev(ndot), dev(R),
+                  None if box is None else dev(box, torch.int32))
+    return g
+
+
+def assert_gamma(gg, go, rtol=GAMMA_RTOL):
+    gg = np.asarray(gg)
+    go = np.asarray(go)
+    assert np.array_equal(gg == 0, go == 0), "zero patterns differ: %d vs %d nonzero" % (
+        np.count_nonzero(gg), np.count_nonzero(go))
+    nz = go != 0
+    if nz.any():
+        rel = np.abs(gg[nz] - go[nz]) / np.abs(go[nz])
+        assert rel.max() <= rtol, "max rel err %.3e" % rel.max()
+
+
+def run_both(w, tab, schedules=("batched", "plain"), cd_srcs=(0,)):
+    n, cell = w["n"], w["cell_cm"]
+    ref = O.raytrace(n, cell, w["nH"], w["xHI"], w["pos"], w["ndot"], w["radius"], tab,
+                     nthreads=8)
+    g = make_gpu(n, cell, w["nH"], w["xHI"], w["pos"], w["ndot"], w["radius"], tab)
+    for sch in schedules:
+        gam = g.raytrace(schedule=sch).cpu().numpy()
+        st = g.stats()
+        assert st["launches"] == 1
+        assert_gamma(gam, ref["gamma"])
+        for s in cd_srcs:
+            cd = g.source_coldens(s, schedule=sch).cpu().numpy()
+            ro = O.raytrace(n, cell, w["nH"], w["xHI"], w["pos"][s:s + 1], w["ndot"][s:s + 1],
+                            w["radius"][s:s + 1], tab, gamma=False, coldens_src=0)
+            if not np.array_equal(cd, ro["coldens"]):
+                bad = np.flatnonzero(cd != ro["coldens"])
+                raise AssertionError(
+                    "column density of source %d not bit-identical (%s): %d cells differ, first "
+                    "%d: %r vs %r; source %r R %r" % (s, sch, bad.size, bad[0], cd[bad[0]],
+                                                      ro["coldens"][bad[0]], w["pos"][s],
+                                                      w["radius"][s]))
+    g.stats()
+    g.close()
+
+
+# ------------------------------------------------------------ small cases
+@pytest.mark.parametrize("spec", ["bb", "grey_exact"])
+def test_single_source_uniform_box(spec):
+    """32^3, 10 Mpc, n_H = 1e-3, x_HI = 1, one 1e54 s^-1 source at the centre, R = 16."""
+    run_both(S.single_source_uniform(), table(spec))
+
+
+@pytest.mark.parametrize("xhi", [5e-5, 1e-10, 1e-12])
+def test_thick_and_thin_regimes(xhi):
+    run_both(S.single_source_uniform(xhi=xhi, radius=15.0), table("grey_exact"))
+    run_both(S.single_source_uniform(xhi=xhi, radius=15.0), table("bb"), schedules=("batched",))
+
+
+def _random_box(n, nsrc, rmax, seed, dup=True):
+    rng = np.random.default_rng(seed)
+    nH = S.lognormal_field(n, 1e-3, sigma_ln=1.0, seed=seed)
+    xHI = rng.uniform(0, 1, (n, n, n)) ** 3  # many nearly ionised cells
+    pos = rng.integers(0, n, (nsrc, 3)).astype(np.int32)
+    pos[0] = (0, n - 1, 0)
+    R = rng.uniform(0.4, rmax, nsrc)
+    ndot = 10 ** rng.uniform(46, 52, nsrc)
+    if dup and nsrc > 4:
+        pos[1] = pos[2]          # co-located, equal radius: merged
+        R[1] = R[2]
+        pos[3] = pos[2]          # co-located, different radius: kept apart
+    return dict(n=n, cell_cm=10 * S.KPC_CM, nH=nH, xHI=xHI, pos=pos, ndot=ndot, radius=R)
+
+
+@pytest.mark.parametrize("n,nsrc,rmax,seed", [(16, 20, 12.0, 1), (17, 30, 25.0, 2),
+                                              (24, 60, 12.0, 3), (9, 5, 40.0, 4)])
+def test_lognormal_boxes_many_sources(n, nsrc, rmax, seed):
+    run_both(_random_box(n, nsrc, rmax, seed), table("bb"), cd_srcs=(0, 1, 3))
+
+
+def test_degenerate_sizes():
+    # one-cell box, radius below one cell, zero rate, huge radius clipped by the window
+    for n, R, nd in [(1, 5.0, 1e50), (8, 0.5, 1e50), (8, 100.0, 0.0), (2, 3.0, 1e49)]:
+        w = dict(n=n, cell_cm=10 * S.KPC_CM, nH=np.full((n, n, n), 1e-3),
+                 xHI=np.full((n, n, n), 1e-4), pos=np.zeros((1, 3), np.int32),
+                 ndot=np.array([nd]), radius=np.array([R]))
+        run_both(w, table("bb"))
+
+
+def test_no_sources_gives_zero_rates():
+    api = A()
+    n = 8
+    g = api.Grid(n, S.KPC_CM)
+    g.set_tables("grey_exact")
+    g.set_density(dev(np.full(n ** 3, 1e-3)))
+    g.set_xHI(dev(np.full(n ** 3, 0.5)))
+    g.set_sources(dev(np.zeros((0, 3)), torch.int32), dev(np.zeros(0)), dev(np.zeros(0)))
+    gam = g.raytrace()
+    assert torch.count_nonzero(gam).item() == 0
+    g.close()
+
+
+def test_ensemble_matches_per_box_oracle():
+    sizes = [12, 17, 20, 9]
+    boxes = [_random_box(n, 6 + b, 9.0, 10 + b, dup=False) for b, n in enumerate(sizes)]
+    cell = boxes[0]["cell_cm"]
+    tab = table("bb")
+    nH = np.concatenate([b["nH"].reshape(-1) for b in boxes])
+    xHI = np.concatenate([b["xHI"].reshape(-1) for b in boxes])
+    pos = np.concatenate([b["pos"] for b in boxes])
+    ndot = np.concatenate([b["ndot"] for b in boxes])
+    R = np.concatenate([b["radius"] for b in boxes])
+    bid = np.concatenate([np.full(len(b["pos"]), i) for i, b in enumerate(boxes)])
+    g = make_gpu(None, cell, nH, xHI, pos, ndot, R, tab, box=bid, sizes=sizes)
+    for sch in ("batched", "plain"):
+        gam = g.raytrace(schedule=sch).cpu().numpy()
+        off = 0
+        for b, bx in zip(sizes, boxes):
+            ref = O.raytrace(b, cell, bx["nH"], bx["xHI"], bx["pos"], bx["ndot"], bx["radius"], tab)
+            assert_gamma(gam[off:off + b ** 3], ref["gamma"])
+            off += b ** 3
+    g.stats()
+    g.close()
+
+
+def test_invalid_inputs_are_rejected():
+    api = A()
+    n = 8
+    g = api.Grid(n, S.KPC_CM)
+    with pytest.raises(api.RtError, match="RT_ERR_STATE"):
+        g.raytrace()
+    g.set_tables("grey_exact")
+    bad = np.full(n ** 3, 1e-3)
+    bad[5] = -1.0
+    with pytest.raises(api.RtError, match="RT_ERR_INVALID"):
+        g.set_density(dev(bad))
+    bad[5] = np.nan
+    with pytest.raises(api.RtError, match="RT_ERR_INVALID"):
+        g.set_density(dev(bad))
+    g.set_density(dev(np.full(n ** 3, 1e-3)))
+    x = np.full(n ** 3, 0.5)
+    x[7] = 1.5
+    with pytest.raises(api.RtError, match="RT_ERR_INVALID"):
+        g.set_xHI(dev(x))
+    g.set_xHI(dev(np.full(n ** 3, 0.5)))
+    with pytest.raises(api.RtError, match="RT_ERR_INVALID"):
+        g.set_sources(dev([[0, 0, 8]], torch.int32), dev([1e50]), dev([3.0]))
+    with pytest.raises(api.RtError, match="RT_ERR_INVALID"):
+        g.set_sources(dev([[0, 0, 0]], torch.int32), dev([1e50]), dev([0.0]))
+    with pytest.raises(api.RtError, match="RT_ERR_INVALID"):
+        g.set_sources(dev([[0, 0, 0]], torch.int32), dev([-1.0]), dev([2.0]))
+    g.set_sources(dev([[1, 2, 3]], torch.int32), dev([1e50]), dev([3.0]))
+    gam = g.raytrace()
+    assert torch.count_nonzero(gam).item() > 0
+    g.close()
+
+
+# -------------------------------------------------------------- chemistry
+def test_chemistry_step_matches_oracle():
+    api = A()
+    n = 24
+    rng = np.random.default_rng(5)
+    nH = S.lognormal_field(n, 1e-3, seed=5).reshape(-1)
+    gam = np.where(rng.uniform(size=n ** 3) < 0.2, 0.0, 10 ** rng.uniform(-16, -11, n ** 3))
+    x0 = rng.uniform(0, 1, n ** 3) ** 2
+    x0[:10] = 0.0
+    xa_in = np.clip(x0 + rng.normal(0, 0.05, n ** 3), 0, 1)
+    dt = 5.0 * S.MYR_S
+    xa_o, xn_o, cnt_o = O.chemistry(nH, x0, xa_in, gam, dt, alpha_H=2.59e-13, C_H=1e-16)
+    g = api.Grid(n, S.KPC_CM)
+    g.set_density(dev(nH))
+    xa, xn, cnt = g.chemistry_step(dev(gam), dev(x0), dev(xa_in), dt, alpha_H=2.59e-13, C_H=1e-16)
+    np.testing.assert_allclose(xa.cpu().numpy(), xa_o, rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(xn.cpu().numpy(), xn_o, rtol=1e-12, atol=1e-300)
+    assert abs(int(cnt.item()) - cnt_o) <= 2
+    g.close()
+
+
+def _oracle_step(n, cell, nH, x, src, ndot, R, tab, dt, iters):
+    xa = x.copy()
+    for _ in range(iters):
+        G = O.raytrace(n, cell, nH, 1.0 - xa, src, ndot, R, tab)["gamma"]
+        xa, xn, _ = O.chemistry(nH, x, xa, G, dt)
+    return xn, G
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_iterate_matches_oracle_fixed_iterations(use_graph):
+    """Test 1 set-up (Sec. 4.1.1) on 16^3: three RT <-> chemistry iterations of one step."""
+    api = A()
+    n = 16
+    cell = 10 * S.KPC_CM / n
+    nH = np.full(n ** 3, 1e-3)
+    x = np.zeros(n ** 3)
+    src = np.array([[8, 8, 8]], np.int32)
+    ndot, R = np.array([1e48]), np.array([7.5])
+    tab = table("grey_exact")
+    dt = 50 * S.MYR_S
+    xo, Go = _oracle_step(n, cell, nH, x, src, ndot, R, tab, dt, 3)
+    g = make_gpu(n, cell, nH, 1.0 - x, src, ndot, R, tab)
+    xd = dev(x)
+    gam, it = g.iterate(xd, dt, max_iter=3, conv_frac=0.0, use_graph=use_graph)
+    assert it == 3
+    np.testing.assert_allclose(xd.cpu().numpy(), xo, rtol=1e-9, atol=1e-300)
+    assert_gamma(gam.cpu().numpy(), Go)
+    # a tolerance every cell meets stops after the first iteration
+    xd2 = dev(x)
+    gam2, it2 = g.iterate(xd2, dt, max_iter=5, conv_frac=1.0, use_graph=use_graph)
+    assert it2 == 1
+    g.close()
