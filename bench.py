@@ -162,8 +162,8 @@ def run_reference(args, rank, world):
                    "sample": "random subsets of the sources per step (%s sources)" % samples},
         "ns_per_source_voxel": 1e9 / value,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "per step a random subset of %s of the %d sources, full 250^3 "
-                                   "fields, OpenMP over sources" % (samples, len(w["ndot"]))},
+                         "sample": "per step a random subset of %s of the %d sources, full %d^3 "
+                                   "fields, OpenMP over sources" % (samples, len(w["ndot"]), args.n)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -338,8 +338,8 @@ def main():
             OB.build()
             rate, cdt, k, csv = oracle_sample(w, args.cpu_seconds, cores)
             cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": "%d random sources of the same 250^3 workload (%.3e source-voxels, "
-                             "%.1f s), OpenMP over sources" % (k, csv, cdt)}
+                   "sample": "%d random sources of the same %d^3 workload (%.3e source-voxels, "
+                             "%.1f s), OpenMP over sources" % (k, n, csv, cdt)}
         except Exception as e:  # the baseline is a report, not a gate
             cpu = {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": "failed: %s" % e}
