@@ -172,6 +172,32 @@ rt_status rt_get_stats(rt_grid_t g, rt_stats* out);
 
 void rt_grid_destroy(rt_grid_t g);
 
+/* Column density (cm^-2) from one source through every traced cell, exactly as
+ * rt_raytrace_source_coldens computes it (bit for bit), for callers that cannot
+ * allocate device memory when they call: code running while someone else
+ * captures a CUDA graph, frameworks that reserve all device memory at start-up
+ * and forbid cudaMalloc afterwards, or loops where an allocation's implicit
+ * synchronisation is not acceptable.  The paper has no counterpart; it is the
+ * plain (octahedral-shell) trace of one source with its scratch cube in a fixed
+ * file-scope device array instead of library-allocated memory.
+ *   n, cell_cm, sigma0_cm2 : box size, cell size (cm), threshold cross section
+ *   d_nH, d_xHI            : device fields (n^3, C order), read only, not validated
+ *   i, j, k, radius        : source cell and radius in cells (> 0)
+ *   d_coldens              : device output, n^3 doubles, fully overwritten
+ *   s                      : stream (NULL = legacy default stream)
+ * Allocates nothing: no cudaMalloc/cudaFree and no allocating library call.  The
+ * traced half-extent min(floor(R), n/2) must not exceed 40 cells (the scratch
+ * array holds one 81^3 cube, 4.25 MB, reserved on every GPU that loads the
+ * library until the process exits); larger requests return RT_ERR_INVALID
+ * before launching anything.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current: make it
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (every cell a call reads it has written first); calls that
+ * overlap on the GPU race on it, so serialise them. */
+rt_status rt_coldens_single_noalloc(int n, double cell_cm, double sigma0_cm2, const double* d_nH,
+                                    const double* d_xHI, int i, int j, int k, double radius,
+                                    double* d_coldens, rt_stream_t s);
+
 /* Number of CUDA kernels this library has launched from host code in this
  * process (kernels replayed by a CUDA graph are counted when captured). */
 long long rt_kernel_launch_count(void);

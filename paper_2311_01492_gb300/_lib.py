@@ -55,6 +55,7 @@ SIGNATURES = {
     "rt_grid_destroy": (None, [_P]),
     "rt_shell_enumerate": (_I, [_I, _P]),
     "rt_kernel_launch_count": (C.c_longlong, []),
+    "rt_coldens_single_noalloc": (_I, [_I, _D, _D, _P, _P, _I, _I, _I, _D, _P, _P]),
 }
 
 
