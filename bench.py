@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--n", type=int, default=250)
     ap.add_argument("--box-mpc", type=float, default=349.0)
     ap.add_argument("--plain-steps", type=int, default=1, help="timed RT_SCHED_PLAIN traces")
+    ap.add_argument("--adjoint-src", type=int, default=100_000,
+                    help="sources of the gradient-throughput measurement (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -202,6 +204,9 @@ def main():
     g.set_xHI(xHI_d)
     dt = 5.0 * 3.15576e13
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    g.set_sources(pos_d, ndot_d, R_d)
+    tuned = g.autotune(os.path.join(ROOT, "gpurun_out", "autotune_cache.txt")
+                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -259,6 +264,30 @@ def main():
         plain = {"trace_ms": pmed, "sv_per_s": w["paper_sv"] / (pmed * 1e-3),
                  "ns_per_source_voxel": pmed * 1e6 / w["paper_sv"],
                  "batched_speedup": pmed / tr_ms}
+
+    # ---------------- adjoint: gradient throughput, 1e5 sources of the same box
+    adjoint = None
+    if args.adjoint_src > 0:
+        k = min(args.adjoint_src, len(w["ndot"]))
+        rng = np.random.default_rng(11)
+        sel = np.sort(rng.choice(len(w["ndot"]), size=k, replace=False))
+        psub, qsub, rsub = pos_d[sel], ndot_d[sel], R_d[sel]
+        wl = torch.tensor(np.random.default_rng(2311_01492 + 4).standard_normal(n ** 3), **f64)
+        g.set_sources(psub, qsub, rsub)
+        sv_sub = float(np.sum(4.0 / 3.0 * math.pi * w["radius"][sel] ** 3))
+        fw, bw = [], []
+        for rep in range(3):
+            flush.fill_(3.0)
+            g.raytrace(gamma, schedule="batched")
+            fw.append(g.stats()["trace_ms"])
+            flush.fill_(4.0)
+            g.backward(wl)
+            bw.append(g.stats()["trace_ms"])
+        adjoint = {"sources": k, "source_voxels_paper": sv_sub,
+                   "forward_trace_ms": min(fw), "backward_ms": min(bw),
+                   "backward_over_forward": min(bw) / min(fw),
+                   "grad_sv_per_s": sv_sub / (min(bw) * 1e-3)}
+        g.set_sources(pos_d, ndot_d, R_d)
 
     # ---------------- end to end through the public API with host buffers
     pin = dict(pin_memory=True)
@@ -323,7 +352,7 @@ def main():
     traffic = None
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved_tf / peak_tf, "traffic": traffic,
-                "kernel": "k_trace_faces (FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "kernel": "k_trace_faces + k_trace_faces_warp (FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz)",
                 "algorithmic_flops_per_launch": flops,
                 "hbm_view": {"achieved_gbs": BYTES_PER_SV * exact_sv / (tr_ms * 1e-3) / 1e9,
                              "peak_gbs": hbm_peak,
@@ -351,7 +380,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], "n": n, "box_mpc": args.box_mpc,
                        "nsrc": len(w["ndot"]), "radius_cells": "5-50 (R=5(Ndot/1e50)^0.2)",
-                       "schedule": "batched (persistent, 6 faces/source, LPT queue)",
+                       "schedule": "batched (persistent, 24 face-quadrant items/source, LPT "
+                                   "queue; autotuned CTA %d threads, warp mode for layer "
+                                   "half-width <= %d)" % tuned,
                        "step": "ingest + dtau + trace + chemistry",
                        "l2": "512 MB write between steps; fields 3 x 125 MB > L2",
                        "per_rank": "independent box per rank (weak scaling)"},
@@ -361,6 +392,7 @@ def main():
                            "ns_per_source_voxel": tr_ms * 1e6 / w["paper_sv"],
                            "rate_cells": statistics.mean(rate_cells)},
             "plain": plain,
+            "adjoint": adjoint,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": world * w["paper_sv"] / (e2e_ms * 1e-3), "unit": UNIT,

@@ -57,7 +57,10 @@ typedef struct {
 enum {
   RT_SCHED_AUTO = 0,    /* batched, with the autotuned (or default) configuration           */
   RT_SCHED_PLAIN = 1,   /* ASORA-style: one CTA per source, octahedral shells S_q in order   */
-  RT_SCHED_BATCHED = 2  /* persistent work queue over (source, face) items, LPT order        */
+  RT_SCHED_BATCHED = 2, /* persistent work queue over (source, face, quadrant) items, LPT   */
+  RT_SCHED_BATCHED_EXIT = 3 /* as BATCHED, but an item stops once a whole layer is opaque
+                               (tau_out >= 2^E1 (1+2^-40) everywhere): the rates are the same
+                               bit for bit, the skipped column densities are not computed    */
 };
 
 /* Rate table kinds for rt_set_tables. */
@@ -151,6 +154,17 @@ rt_status rt_iterate(rt_grid_t g, double* d_x, double dt_s, double alpha_H, doub
                      int max_iter, double conv_tol, double conv_frac, int use_graph,
                      double* d_gamma, int* h_iters);
 
+/* Adjoint of rt_raytrace for L = sum_p w_p Gamma_p with w = d_dL_dgamma (n^3):
+ * writes dL/dlog n_HI of every cell to d_dL_dlog_nHI (n^3, overwritten) and
+ * dL/dlog Ndot of every input source to d_dL_dlog_ndot (nsrc, overwritten;
+ * members of a merged source share its derivative in proportion to their
+ * rates).  n_HI = n_H x_HI enters through dtau and the 1/n_HI of Eq. sugg; the
+ * table lookups are differentiated as the chords they are (exact grey: exp).
+ * Column densities are recomputed per (source, face) item, never stored per
+ * source.  The thin/thick switch is treated as locally constant. */
+rt_status rt_raytrace_backward(rt_grid_t g, const double* d_dL_dgamma, double* d_dL_dlog_nHI,
+                               double* d_dL_dlog_ndot);
+
 /* Timing/launch statistics of the last rt_raytrace on this grid (device event
  * time of the trace kernels, launches, source-voxels traced). */
 typedef struct {
@@ -166,6 +180,21 @@ typedef struct {
   int block;                /* threads per CTA of the trace kernel                  */
   int grid;                 /* CTAs of the trace kernel                             */
 } rt_stats;
+
+/* Schedule of RT_SCHED_BATCHED: items of sources whose largest layer half-width
+ * exceeds hsmall are traced by CTAs of block_big threads (128 or 256), the
+ * others by single warps (hsmall 0..24; 0 = CTAs only); unroll must be 1.
+ * Defaults 128, 19, 1; results do not depend on the choice. */
+rt_status rt_set_schedule(rt_grid_t g, int block_big, int hsmall, int unroll);
+
+/* Autotuner of RT_SCHED_BATCHED: times rt_raytrace on the registered fields and
+ * sources for block_big in {128, 256} and hsmall in {0, 11, 15, 19, 22}, keeps the
+ * fastest and returns it in *h_block, *h_hsmall (either may be NULL).  With a
+ * cache file (may be NULL), a line "<workload key> <block> <hsmall>" whose key
+ * (box sizes, source count and radius distribution) matches is used without
+ * timing, and a new result is appended.  Synchronises; allocates one temporary
+ * rate field. */
+rt_status rt_autotune(rt_grid_t g, const char* cache_path, int* h_block, int* h_hsmall);
 
 /* Statistics of the last trace (synchronises the grid's stream). */
 rt_status rt_get_stats(rt_grid_t g, rt_stats* out);

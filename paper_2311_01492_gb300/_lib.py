@@ -6,7 +6,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libasora.so")
 
 RT_OK, RT_ERR_INVALID, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_TIMEOUT, RT_ERR_STATE = range(6)
-RT_SCHED_AUTO, RT_SCHED_PLAIN, RT_SCHED_BATCHED = 0, 1, 2
+RT_SCHED_AUTO, RT_SCHED_PLAIN, RT_SCHED_BATCHED, RT_SCHED_BATCHED_EXIT = 0, 1, 2, 3
 RT_TABLE_CHORDS, RT_TABLE_GREY_EXACT = 0, 1
 STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_OOM", 3: "RT_ERR_CUDA",
                 4: "RT_ERR_TIMEOUT", 5: "RT_ERR_STATE"}
@@ -52,6 +52,9 @@ SIGNATURES = {
     "rt_chemistry_step": (_I, [_P, _P, _P, _P, _D, _D, _D, _D, _P, _P, _P]),
     "rt_iterate": (_I, [_P, _P, _D, _D, _D, _I, _D, _D, _I, _P, C.POINTER(_I)]),
     "rt_get_stats": (_I, [_P, C.POINTER(rt_stats)]),
+    "rt_set_schedule": (_I, [_P, _I, _I, _I]),
+    "rt_raytrace_backward": (_I, [_P, _P, _P, _P]),
+    "rt_autotune": (_I, [_P, C.c_char_p, C.POINTER(_I), C.POINTER(_I)]),
     "rt_grid_destroy": (None, [_P]),
     "rt_shell_enumerate": (_I, [_I, _P]),
     "rt_kernel_launch_count": (C.c_longlong, []),

@@ -19,7 +19,8 @@ TAU_LIM = 1e-7
 TABLE_E0, TABLE_E1, TABLE_BITS = 30, 14, 6
 ALPHA_B_1E4K = 2.59e-13  # case-B recombination coefficient at 1e4 K (Sec. 4.1.1)
 
-_SCHED = {"auto": L.RT_SCHED_AUTO, "plain": L.RT_SCHED_PLAIN, "batched": L.RT_SCHED_BATCHED}
+_SCHED = {"auto": L.RT_SCHED_AUTO, "plain": L.RT_SCHED_PLAIN, "batched": L.RT_SCHED_BATCHED,
+          "early_exit": L.RT_SCHED_BATCHED_EXIT}
 
 
 def _ptr(t):
@@ -181,6 +182,29 @@ class Grid:
         self._keep.pop("xHI", None)
         return gamma, it.value
 
+    def backward(self, w, dlogn=None, dlogndot=None):
+        """Adjoint of raytrace for L = sum(w * Gamma): (dL/dlog n_HI, dL/dlog Ndot)."""
+        _dev_f64(w, self.ncell, "w")
+        if dlogn is None:
+            dlogn = torch.empty(self.ncell, dtype=torch.float64, device="cuda")
+        if dlogndot is None:
+            dlogndot = torch.empty(max(self.nsrc, 1), dtype=torch.float64, device="cuda")
+        L.check(self._lib.rt_raytrace_backward(self._h, _ptr(w), _ptr(dlogn), _ptr(dlogndot)),
+                "rt_raytrace_backward")
+        return dlogn, dlogndot[:self.nsrc]
+
+    def set_schedule(self, block_big=128, hsmall=19, unroll=1):
+        L.check(self._lib.rt_set_schedule(self._h, int(block_big), int(hsmall), int(unroll)),
+                "rt_set_schedule")
+
+    def autotune(self, cache_path=None):
+        """Pick the batched schedule (CTA size, warp-mode threshold) by timing."""
+        b, hs = C.c_int(0), C.c_int(0)
+        L.check(self._lib.rt_autotune(self._h, None if cache_path is None else
+                                      str(cache_path).encode(), C.byref(b), C.byref(hs)),
+                "rt_autotune")
+        return b.value, hs.value
+
     def stats(self):
         s = L.rt_stats()
         L.check(self._lib.rt_get_stats(self._h, C.byref(s)), "rt_get_stats")
@@ -196,3 +220,37 @@ class Grid:
             self.close()
         except Exception:
             pass
+
+
+class RayTraceFn(torch.autograd.Function):
+    """Gamma as a differentiable function of log n_HI (per cell) and log Ndot (per
+    source); the backward pass is the library's adjoint kernel.  The grid's
+    sources are re-registered with rates exp(log_ndot) and its density with
+    n_H = exp(log_nhi), x_HI = 1 on every call."""
+
+    @staticmethod
+    def forward(ctx, log_nhi, log_ndot, grid, pos, radius, schedule="batched"):
+        nhi = torch.exp(log_nhi).contiguous()
+        ndot = torch.exp(log_ndot).contiguous()
+        ones = torch.ones_like(nhi)
+        grid.set_density(nhi)
+        grid.set_xHI(ones)
+        grid.set_sources(pos, ndot, radius)
+        gamma = grid.raytrace(schedule=schedule)
+        ctx.grid = grid
+        ctx.save_for_backward(nhi, ones, pos, ndot, radius)
+        return gamma
+
+    @staticmethod
+    def backward(ctx, gout):
+        grid = ctx.grid
+        nhi, ones, pos, ndot, radius = ctx.saved_tensors
+        grid.set_density(nhi)
+        grid.set_xHI(ones)
+        grid.set_sources(pos, ndot, radius)
+        dn, dq = grid.backward(gout.contiguous())
+        return dn, dq, None, None, None, None
+
+
+def raytrace_autograd(grid, log_nhi, log_ndot, pos, radius, schedule="batched"):
+    return RayTraceFn.apply(log_nhi, log_ndot, grid, pos, radius, schedule)

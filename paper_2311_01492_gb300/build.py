@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libasora.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["api.cu", "prep.cu", "trace.cu", "chem.cu", "noalloc.cu", "tables.cpp"]
+SOURCES = ["api.cu", "prep.cu", "trace.cu", "adjoint.cu", "chem.cu", "noalloc.cu", "tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-I", INCLUDE,

@@ -3,6 +3,8 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <string>
 
 #include "asora_internal.cuh"
@@ -40,6 +42,7 @@ static void free_grid(Grid* g) {
   cudaFree(g->src_of_input); cudaFree(g->geo); cudaFree(g->queue); cudaFree(g->err);
   cudaFree(g->cube); cudaFree(g->unconv); cudaFree(g->xbuf); cudaFree(g->xavg);
   cudaFree(g->xavg2); cudaFree(g->xhi_int); cudaFree(g->flags); cudaFree(g->counters);
+  cudaFree(g->ndot_in); cudaFree(g->bwd_stack); cudaFree(g->dq_merged);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
   delete g;
@@ -105,6 +108,13 @@ static TraceArgs base_args(Grid& g) {
   a.sigma0 = g.p.sigma0_cm2;
   a.err = g.err;
   a.rate_cells = g.counters;
+  {
+    double tmax;
+    std::memcpy(&tmax, &a.tab.tau_max_bits, 8);
+    const double bound = tmax * (1.0 + std::ldexp(1.0, -40));
+    std::memcpy(&a.exit_bits, &bound, 8);
+  }
+  a.early_exit = 0;
   return a;
 }
 
@@ -118,11 +128,13 @@ static rt_status check_ready(Grid& g, const char* who) {
 // Trace all sources, adding rates into `gamma` (already zeroed) or writing one
 // source's column densities.  `items`/`n_items` select the work.
 static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* items, int n_items,
-                           int schedule, int nsrc_plain, const int* skip = nullptr) {
+                           int schedule, int nsrc_plain, const int* skip = nullptr,
+                           bool early_exit = false) {
   TraceArgs a = base_args(g);
   a.gamma = gamma;
   a.coldens = coldens;
   a.skip = skip;
+  a.early_exit = early_exit ? 1 : 0;
   g.stats.launches = 0;
   TRY(cudaMemsetAsync(g.counters, 0, sizeof(unsigned long long), g.stream));
   if (schedule == RT_SCHED_PLAIN) {
@@ -149,23 +161,62 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
     g.stats.launches = 1;
     g.stats.items = nsrc_plain;
   } else {
-    const int hcap = face_hcap(g.max_r2, g.nmax);
-    const size_t smem = faces_smem_bytes(hcap, 256);
-    if (smem > 227 * 1024)
-      return fail(RT_ERR_INVALID, "rt_raytrace: radius too large for the batched schedule's "
-                                  "shared-memory layers; use RT_SCHED_PLAIN");
-    const int block = 256;
-    const int maxg = faces_max_grid(block, smem);
-    if (maxg <= 0) return fail(RT_ERR_CUDA, "rt_raytrace: no occupancy for the face kernel");
-    const int grid = std::max(1, std::min(n_items, maxg));
-    a.hcap = hcap;
+    // Batched: items of large sources are traced by whole CTAs, items whose
+    // layers fit g.hsmall by single warps (items are in LPT order, so the
+    // warp-mode items are a suffix).
+    const int hbig = face_hcap(g.max_r2, g.nmax);
+    int split = n_items, hsm = 0;
+    if (items == g.items && g.hsmall > 0 && !g.r2_sorted_h.empty()) {
+      int lo = 0, hi = (int)g.r2_sorted_h.size();  // first p with face_hcap(r2[p]) <= hsmall
+      while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (face_hcap(g.r2_sorted_h[mid], g.nmax) <= g.hsmall) hi = mid; else lo = mid + 1;
+      }
+      if (lo < (int)g.r2_sorted_h.size()) {
+        split = std::min(n_items, 24 * lo);
+        hsm = face_hcap(g.r2_sorted_h[lo], g.nmax);
+      }
+    }
+    TRY(cudaMemsetAsync(g.queue, 0, 2 * sizeof(int), g.stream));
     a.items = items;
-    a.n_items = n_items;
-    TRY(cudaMemsetAsync(g.queue, 0, sizeof(int), g.stream));
-    TRY(launch_trace_faces(g, a, block, grid, smem));
-    g.stats.block = block;
-    g.stats.grid = grid;
-    g.stats.launches = 1;
+    g.stats.launches = 0;
+    if (split > 0) {
+      const int block = g.block_big;
+      const size_t smem = faces_smem_bytes(hbig, block);
+      if (smem > 227 * 1024)
+        return fail(RT_ERR_INVALID, "rt_raytrace: radius too large for the batched schedule's "
+                                    "shared-memory layers; use RT_SCHED_PLAIN");
+      const int maxg = faces_max_grid(block, smem, g.unroll);
+      if (maxg <= 0) return fail(RT_ERR_CUDA, "rt_raytrace: no occupancy for the face kernel");
+      TraceArgs b = a;
+      b.hcap = hbig;
+      b.item_begin = 0;
+      b.n_items = split;
+      b.queue = g.queue;
+      const int grid = std::max(1, std::min(split, maxg));
+      TRY(launch_trace_faces(g, b, block, grid, smem, g.unroll));
+      g.stats.block = block;
+      g.stats.grid = grid;
+      g.stats.launches += 1;
+    }
+    if (split < n_items) {
+      const size_t smem = faces_smem_bytes(hsm, 32) * g.warps_per_block;
+      const int maxg = faces_max_grid(32, smem, g.unroll);
+      if (maxg <= 0) return fail(RT_ERR_CUDA, "rt_raytrace: no occupancy for the warp face kernel");
+      TraceArgs b = a;
+      b.hcap = hsm;
+      b.item_begin = split;
+      b.n_items = n_items;
+      b.queue = g.queue + 1;
+      const int nitem = n_items - split;
+      const int grid = std::max(1, std::min((nitem + g.warps_per_block - 1) / g.warps_per_block, maxg));
+      TRY(launch_trace_faces(g, b, 32, grid, smem, g.unroll));
+      g.stats.launches += 1;
+      if (split == 0) {
+        g.stats.block = 32;
+        g.stats.grid = grid;
+      }
+    }
     g.stats.items = n_items;
   }
   g.stats.schedule = schedule;
@@ -232,7 +283,7 @@ rt_status rt_ensemble_create(rt_grid_t* out, int nbox, const int* h_n, const dou
   if (e == cudaSuccess) e = cudaMalloc(&g->dtau, g->ncell * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&g->dtauT, g->ncell * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&g->invn, g->ncell * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&g->queue, 16 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&g->queue, 64 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&g->err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&g->unconv, 16 * sizeof(int64_t));
@@ -335,7 +386,7 @@ rt_status rt_set_xHI(rt_grid_t h, const double* d_xHI) { return set_field(h, d_x
 rt_status rt_set_sources(rt_grid_t h, int nsrc, const int32_t* d_pos, const int32_t* d_box,
                          const double* d_ndot, const double* d_radius) {
   if (!h) return fail(RT_ERR_INVALID, "rt_set_sources: null grid");
-  if (nsrc < 0 || nsrc > (1 << 27)) return fail(RT_ERR_INVALID, "rt_set_sources: bad source count");
+  if (nsrc < 0 || nsrc > (1 << 26)) return fail(RT_ERR_INVALID, "rt_set_sources: bad source count");
   if (nsrc > 0 && (!d_pos || !d_ndot || !d_radius))
     return fail(RT_ERR_INVALID, "rt_set_sources: null source array");
   Grid& g = *reinterpret_cast<Grid*>(h);
@@ -348,7 +399,8 @@ rt_status rt_set_sources(rt_grid_t h, int nsrc, const int32_t* d_pos, const int3
 rt_status rt_raytrace(rt_grid_t h, double* d_gamma, int schedule) {
   if (!h) return fail(RT_ERR_INVALID, "rt_raytrace: null grid");
   if (!d_gamma) return fail(RT_ERR_INVALID, "rt_raytrace: null output");
-  if (schedule != RT_SCHED_AUTO && schedule != RT_SCHED_PLAIN && schedule != RT_SCHED_BATCHED)
+  if (schedule != RT_SCHED_AUTO && schedule != RT_SCHED_PLAIN && schedule != RT_SCHED_BATCHED &&
+      schedule != RT_SCHED_BATCHED_EXIT)
     return fail(RT_ERR_INVALID, "rt_raytrace: unknown schedule");
   Grid& g = *reinterpret_cast<Grid*>(h);
   rt_status st = check_ready(g, "rt_raytrace");
@@ -361,7 +413,8 @@ rt_status rt_raytrace(rt_grid_t h, double* d_gamma, int schedule) {
     if (schedule == RT_SCHED_PLAIN)
       st = run_trace(g, d_gamma, nullptr, nullptr, g.nsrc, RT_SCHED_PLAIN, g.nsrc);
     else
-      st = run_trace(g, d_gamma, nullptr, g.items, 6 * g.nsrc, RT_SCHED_BATCHED, g.nsrc);
+      st = run_trace(g, d_gamma, nullptr, g.items, 24 * g.nsrc, RT_SCHED_BATCHED, g.nsrc, nullptr,
+                     schedule == RT_SCHED_BATCHED_EXIT);
     if (st != RT_OK) return st;
   } else {
     g.stats.launches = 0;
@@ -383,9 +436,9 @@ rt_status rt_raytrace_source_coldens(rt_grid_t h, int src, double* d_coldens, in
   int p = 0;
   TRY(cudaMemcpyAsync(&p, g.src_of_input + src, sizeof(int), cudaMemcpyDeviceToHost, g.stream));
   TRY(cudaStreamSynchronize(g.stream));
-  int hitems[6];
-  for (int f = 0; f < 6; ++f) hitems[f] = (p << 3) | f;
-  TRY(cudaMemcpyAsync(g.queue + 8, hitems, 6 * sizeof(int), cudaMemcpyHostToDevice, g.stream));
+  int hitems[24];
+  for (int q = 0; q < 24; ++q) hitems[q] = (p << 5) | q;
+  TRY(cudaMemcpyAsync(g.queue + 8, hitems, 24 * sizeof(int), cudaMemcpyHostToDevice, g.stream));
   TRY(launch_precompute(g));
   TRY(cudaMemsetAsync(d_coldens, 0, g.ncell * sizeof(double), g.stream));
   if (schedule == RT_SCHED_PLAIN) {
@@ -393,7 +446,7 @@ rt_status rt_raytrace_source_coldens(rt_grid_t h, int src, double* d_coldens, in
     TRY(cudaMemcpyAsync(g.queue + 8, hitems, sizeof(int), cudaMemcpyHostToDevice, g.stream));
     st = run_trace(g, nullptr, d_coldens, g.queue + 8, 1, RT_SCHED_PLAIN, 1);
   } else {
-    st = run_trace(g, nullptr, d_coldens, g.queue + 8, 6, RT_SCHED_BATCHED, 0);
+    st = run_trace(g, nullptr, d_coldens, g.queue + 8, 24, RT_SCHED_BATCHED, 0);
   }
   if (st != RT_OK) return st;
   TRY(cudaStreamSynchronize(g.stream));  // hitems is a stack buffer
@@ -473,7 +526,7 @@ rt_status rt_iterate(rt_grid_t h, double* d_x, double dt_s, double alpha_H, doub
     TRY(launch_zero(d_gamma, g.ncell, skip, g.stream));
     TRY(cudaMemsetAsync(g.unconv, 0, sizeof(int64_t), g.stream));
     if (g.nsrc > 0) {
-      rt_status s2 = run_trace(g, d_gamma, nullptr, g.items, 6 * g.nsrc, RT_SCHED_BATCHED, g.nsrc, skip);
+      rt_status s2 = run_trace(g, d_gamma, nullptr, g.items, 24 * g.nsrc, RT_SCHED_BATCHED, g.nsrc, skip);
       if (s2 != RT_OK) return s2;
     }
     TRY(launch_chemistry(g, d_gamma, d_x, xin, dt_s, alpha_H, C_H, 1e-10, 50, conv_tol, xout,
@@ -528,6 +581,154 @@ rt_status rt_iterate(rt_grid_t h, double* d_x, double dt_s, double alpha_H, doub
     TRY(cudaStreamSynchronize(user));
     iters = fl[1];
     *h_iters = iters;
+  }
+  return RT_OK;
+}
+
+rt_status rt_raytrace_backward(rt_grid_t h, const double* d_dL_dgamma, double* d_dL_dlog_nHI,
+                               double* d_dL_dlog_ndot) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_raytrace_backward: null grid");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  if (!d_dL_dgamma || !d_dL_dlog_nHI)
+    return fail(RT_ERR_INVALID, "rt_raytrace_backward: null pointer");
+  if (g.nsrc_in > 0 && !d_dL_dlog_ndot)
+    return fail(RT_ERR_INVALID, "rt_raytrace_backward: null dL/dlog Ndot output");
+  rt_status st = check_ready(g, "rt_raytrace_backward");
+  if (st != RT_OK) return st;
+  TRY(launch_precompute(g));
+  TRY(cudaMemsetAsync(d_dL_dlog_nHI, 0, g.ncell * sizeof(double), g.stream));
+  if (g.nsrc == 0) return RT_OK;
+  if (g.dq_cap < g.nsrc) {
+    cudaFree(g.dq_merged);
+    g.dq_merged = nullptr;
+    g.dq_cap = 0;
+    TRY(cudaMalloc(&g.dq_merged, g.nsrc * sizeof(double)));
+    g.dq_cap = g.nsrc;
+  }
+  TRY(cudaMemsetAsync(g.dq_merged, 0, g.nsrc * sizeof(double), g.stream));
+  const int hcap = face_hcap(g.max_r2, g.nmax);
+  const int lcap = std::max(1, std::min(isqrt_h(g.max_r2), g.nmax / 2 + 1));
+  const size_t smem = bwd_smem_bytes(hcap, lcap);
+  if (smem > 227 * 1024)
+    return fail(RT_ERR_INVALID, "rt_raytrace_backward: radius too large for the shared-memory layers");
+  const size_t scap = face_stack_cap(g.max_r2, g.nmax);
+  const int maxg = bwd_max_grid(smem);
+  if (maxg <= 0) return fail(RT_ERR_CUDA, "rt_raytrace_backward: no occupancy");
+  const int grid = std::max(1, std::min(24 * g.nsrc, maxg));
+  const size_t need = scap * sizeof(double2) * (size_t)grid;
+  if (need > g.bwd_stack_bytes) {
+    cudaFree(g.bwd_stack);
+    g.bwd_stack = nullptr;
+    g.bwd_stack_bytes = 0;
+    TRY(cudaMalloc(&g.bwd_stack, need));
+    g.bwd_stack_bytes = need;
+  }
+  TraceArgs a = base_args(g);
+  a.items = g.items;
+  a.item_begin = 0;
+  a.n_items = 24 * g.nsrc;
+  a.queue = g.queue;
+  a.hcap = hcap;
+  TRY(cudaMemsetAsync(g.queue, 0, sizeof(int), g.stream));
+  TRY(cudaEventRecord(g.ev[1], g.stream));
+  TRY(launch_trace_bwd(g, a, d_dL_dgamma, d_dL_dlog_nHI, g.dq_merged, g.bwd_stack, scap, lcap,
+                       grid, smem));
+  TRY(cudaEventRecord(g.ev[2], g.stream));
+  TRY(launch_dndot_inputs(g, g.dq_merged, d_dL_dlog_ndot));
+  g.stats.launches = 1;
+  g.stats.block = 256;
+  g.stats.grid = grid;
+  g.stats.items = 24 * g.nsrc;
+  return RT_OK;
+}
+
+rt_status rt_set_schedule(rt_grid_t h, int block_big, int hsmall, int unroll) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_set_schedule: null grid");
+  if (block_big != 128 && block_big != 256)
+    return fail(RT_ERR_INVALID, "rt_set_schedule: block must be 128 or 256");
+  if (unroll != 1) return fail(RT_ERR_INVALID, "rt_set_schedule: unroll must be 1");
+  if (hsmall < 0 || hsmall > 24)
+    return fail(RT_ERR_INVALID, "rt_set_schedule: hsmall must be 0..24");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  g.block_big = block_big;
+  g.hsmall = hsmall;
+  g.unroll = unroll;
+  return RT_OK;
+}
+
+// Key of a workload for the autotuner cache: box sizes and the distribution of
+// traced radii (what the schedule's performance depends on).
+static std::string tune_key(const Grid& g) {
+  std::vector<int> r2 = g.r2_sorted_h;  // descending
+  auto pct = [&](double q) { return r2.empty() ? 0 : r2[(size_t)((1.0 - q) * (r2.size() - 1))]; };
+  std::ostringstream k;
+  k << "nbox=" << g.nbox << ",nmax=" << g.nmax << ",ncell=" << g.ncell << ",nsrc=" << g.nsrc
+    << ",r2max=" << g.max_r2 << ",r2p50=" << pct(0.5) << ",r2p90=" << pct(0.9);
+  return k.str();
+}
+
+rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_hsmall) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_autotune: null grid");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  rt_status st = check_ready(g, "rt_autotune");
+  if (st != RT_OK) return st;
+  const std::string key = tune_key(g);
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string line;
+    while (std::getline(in, line)) {
+      std::istringstream ls(line);
+      std::string k;
+      int b = 0, hs = -1;
+      if ((ls >> k >> b >> hs) && k == key && (b == 128 || b == 256) && hs >= 0 && hs <= 24) {
+        g.block_big = b;
+        g.hsmall = hs;
+        if (h_block) *h_block = b;
+        if (h_hsmall) *h_hsmall = hs;
+        return RT_OK;
+      }
+    }
+  }
+  if (g.nsrc == 0) return RT_OK;
+  double* gam = nullptr;
+  TRY(cudaMalloc(&gam, g.ncell * sizeof(double)));
+  const int blocks[] = {128, 256};
+  const int hss[] = {0, 11, 15, 19, 22};
+  float best = 1e30f;
+  int bb = g.block_big, bh = g.hsmall;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int b : blocks)
+    for (int hs : hss) {
+      g.block_big = b;
+      g.hsmall = hs;
+      float t = 0.f;
+      for (int rep = 0; rep < 2 && st == RT_OK; ++rep) {
+        cudaEventRecord(e0, g.stream);
+        st = rt_raytrace(h, gam, RT_SCHED_BATCHED);
+        cudaEventRecord(e1, g.stream);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&t, e0, e1);
+      }
+      if (st != RT_OK) break;
+      if (t < best) {
+        best = t;
+        bb = b;
+        bh = hs;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(gam);
+  if (st != RT_OK) return st;
+  g.block_big = bb;
+  g.hsmall = bh;
+  if (h_block) *h_block = bb;
+  if (h_hsmall) *h_hsmall = bh;
+  if (cache_path) {
+    std::ofstream out(cache_path, std::ios::app);
+    out << key << " " << bb << " " << bh << "\n";
   }
   return RT_OK;
 }

@@ -62,8 +62,9 @@ struct TraceArgs {
   const SrcDev* src;
   const double* ndot;
   const int* r2lim;      // floor(R^2) per source
-  const int* items;      // (source << 3) | face, LPT order
-  int n_items;
+  const int* items;      // (source << 5) | (face << 2) | quadrant, LPT order
+  int item_begin;        // first item of this launch (the queue counts from here)
+  int n_items;           // one past the last item of this launch
   int* queue;            // work counter
   const GeoEntry* geo;
   int geo_mmax;
@@ -75,6 +76,8 @@ struct TraceArgs {
   int* err;              // error flag (bit mask)
   const int* skip;       // if non-null and *skip != 0 the launch does nothing
   unsigned long long* rate_cells;  // number of rate evaluations (may be null)
+  int early_exit;        // stop an item once a whole layer is opaque (rates only)
+  uint64_t exit_bits;    // bits of the opacity bound 2^E1 (1 + 2^-40)
 };
 
 enum ErrBits { ERR_LAYER_CAP = 1, ERR_GEO = 2, ERR_INPUT = 4, ERR_CUBE = 8 };
@@ -111,8 +114,9 @@ struct Grid {
   SrcDev* src = nullptr;
   double* ndot = nullptr;
   int* r2lim = nullptr;
-  int* items = nullptr;    // 6 per source, LPT order
+  int* items = nullptr;    // 24 (face, quadrant) per source, LPT order
   int* src_of_input = nullptr;  // merged index of each input source
+  double* ndot_in = nullptr;    // input photon rates (for the adjoint of merged sources)
   int max_r2 = 0;
   int64_t source_voxels = 0;
   std::vector<int> r2_sorted_h;  // per merged source (LPT order), host copy
@@ -132,7 +136,15 @@ struct Grid {
   double* xavg2 = nullptr;
   double* xhi_int = nullptr;
   int* flags = nullptr;
+  int block_big = 128;      // threads per CTA for large-source items
+  int hsmall = 19;          // items whose layers fit this half-width run one per warp
+  int warps_per_block = 8;  // warp-mode CTA size (fixed by the kernel template)
+  int unroll = 1;           // cells per thread per pass
   unsigned long long* counters = nullptr;  // [0]: rate evaluations of the last trace
+  double2* bwd_stack = nullptr;  // adjoint: per-CTA (tau_in, tau_out) stacks
+  size_t bwd_stack_bytes = 0;
+  double* dq_merged = nullptr;   // adjoint: dL/dlog Ndot per merged source
+  int dq_cap = 0;
   bool capturing = false;
 
   // stats
@@ -152,10 +164,11 @@ cudaError_t launch_precompute(Grid& g, const int* skip = nullptr);
 cudaError_t launch_zero(double* p, int64_t n, const int* skip, cudaStream_t s);
 cudaError_t launch_validate_fields(Grid& g, const double* nH, const double* xHI);
 cudaError_t launch_geometry(GeoEntry* geo, int mmax, cudaStream_t s);
-cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid, size_t smem);
+cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid, size_t smem,
+                               int unroll);
 cudaError_t launch_trace_shells(Grid& g, const TraceArgs& a, int block, int grid);
-size_t faces_smem_bytes(int hcap, int block);
-int faces_max_grid(int block, size_t smem);
+size_t faces_smem_bytes(int hcap, int block);  // per CTA (block 32: per warp)
+int faces_max_grid(int block, size_t smem, int unroll);
 int shells_max_grid(int block);
 rt_status ingest_sources(Grid& g, int nsrc, const int32_t* d_pos, const int32_t* d_box,
                          const double* d_ndot, const double* d_radius);
@@ -165,6 +178,13 @@ cudaError_t launch_chemistry(Grid& g, const double* gamma, const double* x0, con
                              int64_t* unconv, const int* skip_flag);
 cudaError_t launch_one_minus(const double* x, double* y, int64_t n, const int* skip_flag,
                              cudaStream_t s);
+size_t face_stack_cap(int r2, int nmax);
+size_t bwd_smem_bytes(int hcap, int lcap);
+int bwd_max_grid(size_t smem);
+cudaError_t launch_trace_bwd(Grid& g, const TraceArgs& t, const double* w, double* dlogn,
+                             double* dndot_merged, double2* stack, size_t stack_cap, int lcap,
+                             int grid, size_t smem);
+cudaError_t launch_dndot_inputs(Grid& g, const double* dmerged, double* out);
 cudaError_t launch_conv_check(const int64_t* unconv, int64_t limit, int* flag, cudaStream_t s);
 
 }  // namespace asora

@@ -1,0 +1,149 @@
+// Device helpers shared by the trace and adjoint kernels.
+#pragma once
+
+#include "asora_internal.cuh"
+
+namespace asora {
+
+__device__ __forceinline__ int isqrt_i(int x) {
+  int r = (int)sqrtf((float)x);
+  while (r * r > x) --r;
+  while ((r + 1) * (r + 1) <= x) ++r;
+  return r;
+}
+
+__device__ __forceinline__ int wrapc(int x, int n) {
+  x = x < 0 ? x + n : x;
+  return x >= n ? x - n : x;
+}
+
+__device__ __forceinline__ int sgn_i(int x) { return (x > 0) - (x < 0); }
+
+__device__ __forceinline__ uint64_t bits_of(double x) {
+  return (uint64_t)__double_as_longlong(x);
+}
+
+// Chord table lookup: segment from the IEEE bits of tau (tau >= +0).
+__device__ __forceinline__ double tab_eval(const double2* __restrict__ t, const TabDev& tb,
+                                           double tau) {
+  if (tb.kind == RT_TABLE_GREY_EXACT) return exp(-tau);
+  const uint64_t b = bits_of(tau);
+  if (b >= tb.tau_max_bits) return 0.0;
+  int seg = 0;
+  if (b >= tb.tau_min_bits) {
+    const int e = (int)(b >> 52) - 1023;
+    const int m = (int)((b >> (52 - tb.B)) & (uint64_t)((1 << tb.B) - 1));
+    seg = 1 + ((e + tb.E0) << tb.B) + m;
+  }
+  const double2 c = __ldg(&t[seg]);
+  return fma(c.y, tau, c.x);
+}
+
+// Rate of one cell (photon-conserving, Eq. sugg; thin limit Eq. gammalocal).
+__device__ __forceinline__ double cell_rate(const TraceArgs& a, double nd, double tin, double tout,
+                                            double dcell, double invv_cell, double thin_cell,
+                                            double invn) {
+  if (bits_of(dcell) <= bits_of(a.tau_lim)) {
+    return nd * (tab_eval(a.tab.h, a.tab, tin) * thin_cell);
+  }
+  const double dg = tab_eval(a.tab.g, a.tab, tin) - tab_eval(a.tab.g, a.tab, tout);
+  return nd * (dg * invv_cell * invn);
+}
+
+// Slope of the table at tau (derivative of the lookup): the chord slope c1
+// of tau's segment, 0 at and beyond the table's upper bound; -exp(-tau) for
+// exact grey opacity.
+__device__ __forceinline__ double tab_slope(const double2* __restrict__ t, const TabDev& tb,
+                                            double tau) {
+  if (tb.kind == RT_TABLE_GREY_EXACT) return -exp(-tau);
+  const uint64_t b = bits_of(tau);
+  if (b >= tb.tau_max_bits) return 0.0;
+  int seg = 0;
+  if (b >= tb.tau_min_bits) {
+    const int e = (int)(b >> 52) - 1023;
+    const int m = (int)((b >> (52 - tb.B)) & (uint64_t)((1 << tb.B) - 1));
+    seg = 1 + ((e + tb.E0) << tb.B) + m;
+  }
+  return __ldg(&t[seg]).y;
+}
+
+// Shared memory of one group (a CTA, or one warp in warp mode) tracing a
+// quadrant of a face with layer half-width capacity h: two layers of (h+1)^2
+// doubles, and two sets of row tables (the current layer's and the next's):
+// first flat index of every row (h+2 ints) and the row of every flat index
+// (bytes; rows < 256 since h <= 254).
+__host__ __device__ inline size_t group_smem_bytes(int h) {
+  const size_t cap = (size_t)(h + 1) * (h + 1);
+  const size_t b = 2 * cap * sizeof(double) + 2 * (size_t)(h + 2) * sizeof(int) + 2 * cap;
+  return (b + 15) & ~(size_t)15;
+}
+
+template <int GS>
+__device__ __forceinline__ void group_sync() {
+  if (GS == 32) __syncwarp(); else __syncthreads();
+}
+
+// Row table of one quadrant layer: rows a1 = 0..nrows-1 (|t1|), row a1 holds
+// a2 = 0..min(w, lim2) with w = min(H, floor(sqrt(rem - a1^2))).  rowpre[a1] is
+// the first flat index of row a1, rowpre[nrows] the layer size; rowof[t] the
+// row of flat index t.  Ends with the group synchronised.
+template <int GS>
+__device__ __forceinline__ void quad_rows(int rem, int H, int nrows, int lim2,
+                                          int* __restrict__ rowpre,
+                                          unsigned char* __restrict__ rowof, int gt) {
+  constexpr int NW = GS / 32;
+  const int lane = gt & 31, wid = gt >> 5;
+  if (wid == 0) {
+    const int per = (nrows + 31) >> 5;
+    const int rb = lane * per, re = min(nrows, rb + per);
+    int local = 0;
+    for (int r = rb; r < re; ++r) local += min(min(H, isqrt_i(rem - r * r)), lim2) + 1;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    int run = incl - local;
+    for (int r = rb; r < re; ++r) {
+      rowpre[r] = run;
+      run += min(min(H, isqrt_i(rem - r * r)), lim2) + 1;
+    }
+    if (lane == 31) rowpre[nrows] = incl;
+  }
+  group_sync<GS>();
+  for (int r = wid; r < nrows; r += NW) {
+    const int p0 = rowpre[r], len = rowpre[r + 1] - p0;
+    for (int c = lane; c < len; c += 32) rowof[p0 + c] = (unsigned char)r;
+  }
+  group_sync<GS>();
+}
+
+// Row tables of one quadrant layer built by a single warp (lane = 0..31), no
+// synchronisation: rowpre[a1] = first flat index of row a1, rowpre[nrows] =
+// layer size, rowof[t] = row of flat index t.  Each lane handles a contiguous
+// block of rows, so its rowof writes are one contiguous range.
+__device__ __forceinline__ void quad_rows_warp(int rem, int H, int nrows, int lim2,
+                                               int* __restrict__ rowpre,
+                                               unsigned char* __restrict__ rowof, int lane) {
+  const int per = (nrows + 31) >> 5;
+  const int rb = lane * per, re = min(nrows, rb + per);
+  int local = 0;
+  for (int r = rb; r < re; ++r) local += min(min(H, isqrt_i(rem - r * r)), lim2) + 1;
+  int incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  int run = incl - local;
+  for (int r = rb; r < re; ++r) {
+    rowpre[r] = run;
+    const int len = min(min(H, isqrt_i(rem - r * r)), lim2) + 1;
+    for (int c = 0; c < len; ++c) rowof[run + c] = (unsigned char)r;
+    run += len;
+  }
+  if (lane == 31) rowpre[nrows] = incl;
+}
+
+}  // namespace asora

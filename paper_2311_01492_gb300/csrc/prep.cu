@@ -200,7 +200,7 @@ __global__ void k_src_merge(const uint64_t* __restrict__ keys, const int* __rest
   lval[m] = m;
 }
 
-// Permute merged sources into LPT order and emit 6 face items per source.
+// Permute merged sources into LPT order and emit 24 (face, quadrant) items per source.
 __global__ void k_src_order(const int* __restrict__ order, int nm, const SrcDev* __restrict__ msrc,
                             const double* __restrict__ mndot, const int* __restrict__ mr2,
                             SrcDev* __restrict__ src, double* __restrict__ ndot,
@@ -213,7 +213,7 @@ __global__ void k_src_order(const int* __restrict__ order, int nm, const SrcDev*
   ndot[p] = mndot[m];
   r2lim[p] = mr2[m];
   lpt_of_merged[m] = p;
-  for (int f = 0; f < 6; ++f) items[6 * p + f] = (p << 3) | f;
+  for (int q = 0; q < 24; ++q) items[24 * p + q] = (p << 5) | q;  // face = q >> 2, quadrant = q & 3
 }
 
 __global__ void k_remap(int* __restrict__ a, const int* __restrict__ map, int n) {
@@ -266,7 +266,9 @@ rt_status ingest_sources(Grid& g, int nsrc, const int32_t* d_pos, const int32_t*
 
   // free previous sources
   cudaFree(g.src); cudaFree(g.ndot); cudaFree(g.r2lim); cudaFree(g.items); cudaFree(g.src_of_input);
+  cudaFree(g.ndot_in);
   g.src = nullptr; g.ndot = nullptr; g.r2lim = nullptr; g.items = nullptr; g.src_of_input = nullptr;
+  g.ndot_in = nullptr;
   g.nsrc = 0; g.nsrc_in = 0; g.max_r2 = 0; g.source_voxels = 0; g.r2_sorted_h.clear();
   if (nsrc == 0) return RT_OK;
 
@@ -323,6 +325,8 @@ rt_status ingest_sources(Grid& g, int nsrc, const int32_t* d_pos, const int32_t*
   CK(cudaMalloc(&order, nm * sizeof(int)));
   CK(cudaMalloc(&lpt_of_merged, nm * sizeof(int)));
   CK(cudaMalloc(&g.src_of_input, nsrc * sizeof(int)));
+  CK(cudaMalloc(&g.ndot_in, nsrc * sizeof(double)));
+  CK(cudaMemcpyAsync(g.ndot_in, d_ndot, nsrc * sizeof(double), cudaMemcpyDeviceToDevice, s));
   k_src_merge<<<nb, T, 0, s>>>(keys2, idx2, head, mid, nsrc, d_pos, d_box, d_ndot, r2in, msrc,
                                mndot, mr2, lkey, lval, g.src_of_input, g.max_r2);
   count_launch();
@@ -332,7 +336,7 @@ rt_status ingest_sources(Grid& g, int nsrc, const int32_t* d_pos, const int32_t*
   CK(cudaMalloc(&g.src, nm * sizeof(SrcDev)));
   CK(cudaMalloc(&g.ndot, nm * sizeof(double)));
   CK(cudaMalloc(&g.r2lim, nm * sizeof(int)));
-  CK(cudaMalloc(&g.items, (size_t)6 * nm * sizeof(int)));
+  CK(cudaMalloc(&g.items, (size_t)24 * nm * sizeof(int)));
   k_src_order<<<(nm + T - 1) / T, T, 0, s>>>(order, nm, msrc, mndot, mr2, g.src, g.ndot, g.r2lim,
                                              g.items, lpt_of_merged);
   count_launch();

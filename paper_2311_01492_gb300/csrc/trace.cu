@@ -32,204 +32,139 @@
 #include <cmath>
 
 #include "asora_internal.cuh"
+#include "device_util.cuh"
 
 namespace asora {
 
-__device__ __forceinline__ int isqrt_i(int x) {
-  int r = (int)sqrtf((float)x);
-  while (r * r > x) --r;
-  while ((r + 1) * (r + 1) <= x) ++r;
-  return r;
+// ----------------------------------------------------------- face kernels
+size_t faces_smem_bytes(int hcap, int block) {
+  return block == 32 ? group_smem_bytes(hcap) : group_smem_bytes(hcap);
 }
 
-__device__ __forceinline__ int wrapc(int x, int n) {
-  x = x < 0 ? x + n : x;
-  return x >= n ? x - n : x;
-}
-
-__device__ __forceinline__ int sgn_i(int x) { return (x > 0) - (x < 0); }
-
-__device__ __forceinline__ uint64_t bits_of(double x) {
-  return (uint64_t)__double_as_longlong(x);
-}
-
-// Chord table lookup: segment from the IEEE bits of tau (tau >= +0).
-__device__ __forceinline__ double tab_eval(const double2* __restrict__ t, const TabDev& tb,
-                                           double tau) {
-  if (tb.kind == RT_TABLE_GREY_EXACT) return exp(-tau);
-  const uint64_t b = bits_of(tau);
-  if (b >= tb.tau_max_bits) return 0.0;
-  int seg = 0;
-  if (b >= tb.tau_min_bits) {
-    const int e = (int)(b >> 52) - 1023;
-    const int m = (int)((b >> (52 - tb.B)) & (uint64_t)((1 << tb.B) - 1));
-    seg = 1 + ((e + tb.E0) << tb.B) + m;
-  }
-  const double2 c = __ldg(&t[seg]);
-  return fma(c.y, tau, c.x);
-}
-
-// Rate of one cell (photon-conserving, Eq. sugg; thin limit Eq. gammalocal).
-__device__ __forceinline__ double cell_rate(const TraceArgs& a, double nd, double tin, double tout,
-                                            double dcell, double invv_cell, double thin_cell,
-                                            double invn) {
-  if (bits_of(dcell) <= bits_of(a.tau_lim)) {
-    return nd * (tab_eval(a.tab.h, a.tab, tin) * thin_cell);
-  }
-  const double dg = tab_eval(a.tab.g, a.tab, tin) - tab_eval(a.tab.g, a.tab, tout);
-  return nd * (dg * invv_cell * invn);
-}
-
-// ----------------------------------------------------------- face kernel
-size_t faces_smem_bytes(int hcap, int /*block*/) {
-  const size_t cap = (size_t)(2 * hcap + 1) * (2 * hcap + 1);
-  return 2 * cap * sizeof(double) + (size_t)(2 * hcap + 4) * sizeof(int);
-}
-
-template <int BLOCK, bool COLDENS>
-__global__ void __launch_bounds__(BLOCK) k_trace_faces(TraceArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_item;
-  __shared__ int s_total;
-  const int hcap = a.hcap;
-  const int cap = (2 * hcap + 1) * (2 * hcap + 1);
-  double* buf0 = reinterpret_cast<double*>(smem_raw);
+// Trace one (source, face, quadrant) item with a group of GS threads (gt =
+// thread index in the group).  Within a face, a cell's interpolants never
+// cross the lines t1 = 0 or t2 = 0 towards the other side, so each quadrant
+// (sign of t1, sign of t2, the lines included) depends only on itself; the
+// lines are traced by both neighbouring quadrants and owned by the + side.
+// Layers m = 1..Lmax; every cell reads only layer m-1.
+template <int GS, bool COLDENS>
+__device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int item, const int gt,
+                                                unsigned char* __restrict__ sm, const int h,
+                                                unsigned& nrate) {
+  const int cap = (h + 1) * (h + 1);
+  double* buf0 = reinterpret_cast<double*>(sm);
   double* buf1 = buf0 + cap;
-  int* rowpre = reinterpret_cast<int*>(buf1 + cap);
-  const int tid = threadIdx.x;
-  if (a.skip && *a.skip) return;
-  for (int t = tid; t < 2 * cap; t += BLOCK) buf0[t] = 0.0;
-  unsigned nrate = 0;
+  int* rowpre2 = reinterpret_cast<int*>(buf1 + cap);                       // [2][h+2]
+  unsigned char* rowof2 = reinterpret_cast<unsigned char*>(rowpre2 + 2 * (h + 2));  // [2][cap]
+  const int wid = gt >> 5, lane = gt & 31;
 
-  for (;;) {
-    __syncthreads();
-    if (tid == 0) s_item = atomicAdd(a.queue, 1);
-    __syncthreads();
-    const int it = s_item;
-    if (it >= a.n_items) {
-      if (a.rate_cells) {
-        for (int o = 16; o > 0; o >>= 1) nrate += __shfl_down_sync(0xffffffffu, nrate, o);
-        if ((tid & 31) == 0 && nrate) atomicAdd(a.rate_cells, (unsigned long long)nrate);
-      }
+  const int s = item >> 5, f = (item >> 2) & 7, quad = item & 3;
+  const SrcDev S = a.src[s];
+  const BoxDev B = a.boxes[S.box];
+  const int N = B.n;
+  const int R2 = a.r2lim[s];
+  const double nd = a.ndot[s];
+  const int d = f >> 1;
+  const int sg = (f & 1) ? -1 : 1;
+  const int q1 = (quad & 1) ? -1 : 1, q2 = (quad & 2) ? -1 : 1;
+  const int lim1 = q1 > 0 ? B.whi : -B.wlo, lim2 = q2 > 0 ? B.whi : -B.wlo;
+  int Lmax = sg > 0 ? B.whi : -B.wlo;
+  Lmax = min(Lmax, isqrt_i(R2));
+  const int64_t scell = B.off + ((int64_t)S.i * N + S.j) * N + S.k;
+  const double dts = a.dtau[scell];
+
+  if (f == 4 && quad == 0 && gt == 0) {  // the source cell (q = 0), once per source
+    const double tout = 0.5 * dts;
+    if (COLDENS) {
+      a.coldens[scell] = tout / a.sigma0;
+    } else {
+      double dG;
+      if (bits_of(tout) <= bits_of(a.tau_lim))
+        dG = nd * (tab_eval(a.tab.h, a.tab, 0.0) * (0.5 * B.thin_fac));
+      else
+        dG = nd * ((tab_eval(a.tab.g, a.tab, 0.0) - tab_eval(a.tab.g, a.tab, tout)) *
+                   B.inv_cell3 * a.invn[scell]);
+      ++nrate;
+      if (dG != 0.0) atomicAdd(&a.gamma[scell], dG);
+    }
+  }
+
+  // transverse axes (t1, t2) in increasing axis order, and the field layouts:
+  //   z faces read dtauT (k,i,j): index = k N^2 + i N + j  (t1 = i, t2 = j)
+  //   y faces read dtau  (i,j,k): index = i N^2 + j N + k  (t1 = i, t2 = k)
+  //   x faces read dtau  (i,j,k): index = i N^2 + j N + k  (t1 = j, t2 = k)
+  const int64_t NN = (int64_t)N * N;
+  const int c1 = d == 0 ? S.j : S.i;           // source coordinate along t1
+  const int c2 = d == 2 ? S.j : S.k;           // source coordinate along t2
+  const int cd = d == 0 ? S.i : (d == 1 ? S.j : S.k);
+  const int64_t m1 = d == 0 ? (int64_t)N : (d == 1 ? NN : (int64_t)N);  // stride of t1
+  const int64_t md = d == 0 ? NN : (d == 1 ? (int64_t)N : NN);          // stride of the layer axis
+  const double* __restrict__ fld = (d == 2 ? a.dtauT : a.dtau) + B.off;
+
+  double* prev = buf0;
+  double* cur = buf1;
+  int Hp = 0;
+  const bool exit_ok = !COLDENS && a.early_exit;
+  // row tables of layer 1; layer m+1's are built by warp 0 during layer m
+  if (Lmax >= 1 && wid == 0) {
+    const int H1 = min(1, isqrt_i(R2 - 1));
+    if (H1 <= h) quad_rows_warp(R2 - 1, H1, min(H1, lim1) + 1, lim2, rowpre2 + (h + 2), rowof2 + cap, lane);
+  }
+  group_sync<GS>();
+  for (int m = 1; m <= Lmax; ++m) {
+    const int rem = R2 - m * m;
+    const int H = min(m, isqrt_i(rem));
+    if (H > h || m > a.geo_mmax) {
+      if (gt == 0) atomicOr(a.err, H > h ? ERR_LAYER_CAP : ERR_GEO);
       break;
     }
-    const int item = a.items[it];
-    const int s = item >> 3, f = item & 7;
-    const SrcDev S = a.src[s];
-    const BoxDev B = a.boxes[S.box];
-    const int N = B.n;
-    const int R2 = a.r2lim[s];
-    const double nd = a.ndot[s];
-    const int d = f >> 1;
-    const int sg = (f & 1) ? -1 : 1;
-    int Lmax = sg > 0 ? B.whi : -B.wlo;
-    Lmax = min(Lmax, isqrt_i(R2));
-    const int64_t scell = B.off + ((int64_t)S.i * N + S.j) * N + S.k;
-    const double dts = a.dtau[scell];
-
-    if (f == 4 && tid == 0) {  // the source cell (q = 0), once per source
-      const double tout = 0.5 * dts;
-      if (COLDENS) {
-        a.coldens[scell] = tout / a.sigma0;
+    const int nrows = min(H, lim1) + 1;
+    const int* rowpre = rowpre2 + (m & 1) * (h + 2);
+    const unsigned char* rowof = rowof2 + (m & 1) * cap;
+    const int total = rowpre[nrows];
+    const int W = H + 1, Wp = Hp + 1;
+    const int lc = wrapc(cd + sg * m, N);
+    const int64_t lay = (int64_t)lc * md;
+    const int gbase = (int)geo_index(m, 0, 0);
+    bool opaque = true;  // every cell of this thread has tau_out >= the exit bound
+    for (int t = gt; t < total; t += GS) {
+      const int a1 = rowof[t];
+      const int a2 = t - rowpre[a1];
+      const int x1 = wrapc(c1 + q1 * a1, N), x2 = wrapc(c2 + q2 * a2, N);
+      const int64_t gidx = lay + x1 * m1 + x2;
+      const double dtp = __ldg(&fld[gidx]);
+      const int glo = min(a1, a2), ghi = max(a1, a2);
+      const GeoEntry* ge = &a.geo[gbase + ((ghi * (ghi + 1)) >> 1) + glo];
+      const double2 wv0 = __ldg(reinterpret_cast<const double2*>(ge));      // w1, wa
+      const double2 wv1 = __ldg(reinterpret_cast<const double2*>(ge) + 1);  // wb, w4
+      const double ds = __ldg(&ge->ds);
+      double tin;
+      if (m == 1) {
+        tin = (0.5 * dts) * ds;
       } else {
-        double dG;
-        if (bits_of(tout) <= bits_of(a.tau_lim))
-          dG = nd * (tab_eval(a.tab.h, a.tab, 0.0) * (0.5 * B.thin_fac));
-        else
-          dG = nd * ((tab_eval(a.tab.g, a.tab, 0.0) - tab_eval(a.tab.g, a.tab, tout)) *
-                     B.inv_cell3 * a.invn[scell]);
-        if (dG != 0.0) atomicAdd(&a.gamma[scell], dG);
-      }
-    }
-
-    double* prev = buf0;
-    double* cur = buf1;
-    int Hp = 0;
-    for (int m = 1; m <= Lmax; ++m) {
-      const int rem = R2 - m * m;
-      const int H = min(m, isqrt_i(rem));
-      if (H > hcap) {
-        if (tid == 0) atomicOr(a.err, ERR_LAYER_CAP);
-        break;
-      }
-      if (m > a.geo_mmax) {
-        if (tid == 0) atomicOr(a.err, ERR_GEO);
-        break;
-      }
-      const int u0 = max(-H, B.wlo), u1 = min(H, B.whi);
-      const int nrows = u1 - u0 + 1;
-      if (tid < 32) {  // row lengths of the layer and their prefix sums
-        const int per = (nrows + 31) >> 5;
-        const int rb = tid * per, re = min(nrows, rb + per);
-        int local = 0;
-        for (int r = rb; r < re; ++r) {
-          const int t1 = u0 + r;
-          const int w = min(H, isqrt_i(rem - t1 * t1));
-          local += min(w, B.whi) - max(-w, B.wlo) + 1;
-        }
-        int incl = local;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(0xffffffffu, incl, o);
-          if (tid >= o) incl += v;
-        }
-        int run = incl - local;
-        for (int r = rb; r < re; ++r) {
-          rowpre[r] = run;
-          const int t1 = u0 + r;
-          const int w = min(H, isqrt_i(rem - t1 * t1));
-          run += min(w, B.whi) - max(-w, B.wlo) + 1;
-        }
-        if (tid == 31) s_total = incl;
-      }
-      __syncthreads();
-      const int total = s_total;
-      const int W = 2 * H + 1, Wp = 2 * Hp + 1;
-      for (int t = tid; t < total; t += BLOCK) {
-        int lo = 0, hi = nrows - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (rowpre[mid] <= t) lo = mid; else hi = mid - 1;
-        }
-        const int t1 = u0 + lo;
-        const int w = min(H, isqrt_i(rem - t1 * t1));
-        const int t2 = max(-w, B.wlo) + (t - rowpre[lo]);
-        int di, dj, dk;
-        if (d == 2) { di = t1; dj = t2; dk = sg * m; }
-        else if (d == 1) { di = t1; dj = sg * m; dk = t2; }
-        else { di = sg * m; dj = t1; dk = t2; }
-        const int ii = wrapc(S.i + di, N), jj = wrapc(S.j + dj, N), kk = wrapc(S.k + dk, N);
-        const int64_t cell = B.off + ((int64_t)ii * N + jj) * N + kk;
-        const double dtp = (d == 2) ? __ldg(&a.dtauT[B.off + ((int64_t)kk * N + ii) * N + jj])
-                                    : __ldg(&a.dtau[cell]);
-        const int at1 = abs(t1), at2 = abs(t2);
-        const int glo = min(at1, at2), ghi = max(at1, at2);
-        const GeoEntry* ge = &a.geo[geo_index(m, glo, ghi)];
-        const double2 wv0 = __ldg(reinterpret_cast<const double2*>(ge));      // w1, wa
-        const double2 wv1 = __ldg(reinterpret_cast<const double2*>(ge) + 1);  // wb, w4
-        const double ds = __ldg(&ge->ds);
         const double w1 = wv0.x, w4 = wv1.y;
-        const double w2 = at1 <= at2 ? wv0.y : wv1.x;
-        const double w3 = at1 <= at2 ? wv1.x : wv0.y;
-        double tin;
-        if (m == 1) {
-          tin = (0.5 * dts) * ds;
-        } else {
-          const int s1 = sgn_i(t1), s2 = sgn_i(t2);
-          const int a1 = min(max(t1, -Hp), Hp) + Hp, a2 = min(max(t1 - s1, -Hp), Hp) + Hp;
-          const int b1 = min(max(t2, -Hp), Hp) + Hp, b2 = min(max(t2 - s2, -Hp), Hp) + Hp;
-          const double c1 = prev[a1 * Wp + b1];
-          const double c2 = prev[a2 * Wp + b1];
-          const double c3 = prev[a1 * Wp + b2];
-          const double c4 = prev[a2 * Wp + b2];
-          tin = fma(w4, c4, fma(w3, c3, fma(w2, c2, w1 * c1)));
-        }
-        const double tout = fma(dtp, ds, tin);
-        cur[(t1 + H) * W + (t2 + H)] = tout;
-        const bool own = (d == 2) || (d == 1 ? at2 < m : (at1 < m && at2 < m));
+        const double w2 = a1 <= a2 ? wv0.y : wv1.x;
+        const double w3 = a1 <= a2 ? wv1.x : wv0.y;
+        const int b1 = min(a1, Hp), b2 = min(a1 - (a1 > 0), Hp);
+        const int e1 = min(a2, Hp), e2 = min(a2 - (a2 > 0), Hp);
+        const double v1 = prev[b1 * Wp + e1];
+        const double v2 = prev[b2 * Wp + e1];
+        const double v3 = prev[b1 * Wp + e2];
+        const double v4 = prev[b2 * Wp + e2];
+        tin = fma(w4, v4, fma(w3, v3, fma(w2, v2, w1 * v1)));
+      }
+      const double tout = fma(dtp, ds, tin);
+      cur[a1 * W + a2] = tout;
+      opaque = opaque && bits_of(tout) >= a.exit_bits;
+      const bool own = ((d == 2) || (d == 1 ? a2 < m : (a1 < m && a2 < m))) &&
+                       (a1 > 0 || q1 > 0) && (a2 > 0 || q2 > 0);
+      if (!own) continue;
+      if (COLDENS || bits_of(tin) < a.tab.tau_max_bits) {
+        // C-order index of the cell (the z faces gathered from the rotated copy)
+        const int64_t cell = B.off + (d == 2 ? ((int64_t)x1 * N + x2) * N + lc : gidx);
         if (COLDENS) {
-          if (own) a.coldens[cell] = tout / a.sigma0;
-        } else if (own && bits_of(tin) < a.tab.tau_max_bits) {
+          a.coldens[cell] = tout / a.sigma0;
+        } else {
           const double dcell = dtp * ds;
           const double dG = cell_rate(a, nd, tin, tout, dcell, __ldg(&ge->invv) * B.inv_cell3,
                                       __ldg(&ge->thin) * B.thin_fac,
@@ -238,66 +173,127 @@ __global__ void __launch_bounds__(BLOCK) k_trace_faces(TraceArgs a) {
           if (dG != 0.0) atomicAdd(&a.gamma[cell], dG);
         }
       }
-      __syncthreads();
-      double* tmp = prev;
-      prev = cur;
-      cur = tmp;
-      Hp = H;
     }
+    if (wid == 0 && m < Lmax) {  // row tables of the next layer
+      const int rn = R2 - (m + 1) * (m + 1);
+      const int Hn = min(m + 1, isqrt_i(rn));
+      if (Hn <= h)
+        quad_rows_warp(rn, Hn, min(Hn, lim1) + 1, lim2, rowpre2 + ((m + 1) & 1) * (h + 2),
+                       rowof2 + ((m + 1) & 1) * cap, lane);
+    }
+    if (exit_ok) {
+      // Exact early exit: if every cell of this layer has tau_out >= 2^E1 (1 + 2^-40),
+      // every later tau_in (a convex combination plus non-negative increments,
+      // rounding covered by the margin) is >= 2^E1 and all later rates are 0.
+      bool all_opaque;
+      if (GS == 32) {
+        __syncwarp();
+        all_opaque = __all_sync(0xffffffffu, opaque);
+      } else {
+        all_opaque = __syncthreads_and(opaque) != 0;
+      }
+      if (all_opaque) break;
+    } else {
+      group_sync<GS>();
+    }
+    double* tmp = prev;
+    prev = cur;
+    cur = tmp;
+    Hp = H;
   }
 }
 
-template <int BLOCK>
-static cudaError_t launch_faces_t(const TraceArgs& a, int grid, size_t smem, cudaStream_t s,
-                                  bool coldens) {
-  cudaError_t e;
-  if (coldens) {
-    e = cudaFuncSetAttribute(k_trace_faces<BLOCK, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_trace_faces<BLOCK, true><<<grid, BLOCK, smem, s>>>(a);
-    count_launch();
-  } else {
-    e = cudaFuncSetAttribute(k_trace_faces<BLOCK, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_trace_faces<BLOCK, false><<<grid, BLOCK, smem, s>>>(a);
-    count_launch();
-  }
-  return cudaGetLastError();
+__device__ __forceinline__ void flush_rate_count(const TraceArgs& a, unsigned nrate) {
+  if (!a.rate_cells) return;
+  for (int o = 16; o > 0; o >>= 1) nrate += __shfl_down_sync(0xffffffffu, nrate, o);
+  if ((threadIdx.x & 31) == 0 && nrate) atomicAdd(a.rate_cells, (unsigned long long)nrate);
 }
 
-cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid, size_t smem) {
-  const bool cd = a.coldens != nullptr;
+// CTA mode: the whole CTA traces one item at a time (large sources).
+template <int BLOCK, bool COLDENS>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_trace_faces(TraceArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  if (a.skip && *a.skip) return;
+  const int cap = (a.hcap + 1) * (a.hcap + 1);
+  double* buf = reinterpret_cast<double*>(smem_raw);
+  for (int t = threadIdx.x; t < 2 * cap; t += BLOCK) buf[t] = 0.0;
+  unsigned nrate = 0;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = a.item_begin + atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= a.n_items) break;
+    trace_face_item<BLOCK, COLDENS>(a, a.items[it], threadIdx.x, smem_raw, a.hcap, nrate);
+  }
+  flush_rate_count(a, nrate);
+}
+
+// Warp mode: every warp traces its own items (small sources), with its own
+// slice of shared memory and warp-level synchronisation only.
+template <int WPB, bool COLDENS>
+__global__ void __launch_bounds__(WPB * 32, 1024 / (WPB * 32)) k_trace_faces_warp(TraceArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (a.skip && *a.skip) return;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* my = smem_raw + (size_t)wid * group_smem_bytes(a.hcap);
+  const int cap = (a.hcap + 1) * (a.hcap + 1);
+  double* buf = reinterpret_cast<double*>(my);
+  for (int t = lane; t < 2 * cap; t += 32) buf[t] = 0.0;
+  __syncwarp();
+  unsigned nrate = 0;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = a.item_begin + atomicAdd(a.queue, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= a.n_items) break;
+    trace_face_item<32, COLDENS>(a, a.items[it], lane, my, a.hcap, nrate);
+    __syncwarp();
+  }
+  flush_rate_count(a, nrate);
+}
+
+constexpr int kWarpsPerBlock = 8;
+
+// Kernel variant for (block, coldens); block 32 = warp mode.  Null if not
+// instantiated.
+static const void* face_kernel(int block, int /*unroll*/, bool coldens) {
   switch (block) {
-    case 64: return launch_faces_t<64>(a, grid, smem, g.stream, cd);
-    case 128: return launch_faces_t<128>(a, grid, smem, g.stream, cd);
-    case 256: return launch_faces_t<256>(a, grid, smem, g.stream, cd);
-    case 512: return launch_faces_t<512>(a, grid, smem, g.stream, cd);
-    default: return cudaErrorInvalidValue;
+    case 32: return coldens ? (const void*)k_trace_faces_warp<kWarpsPerBlock, true>
+                            : (const void*)k_trace_faces_warp<kWarpsPerBlock, false>;
+    case 128: return coldens ? (const void*)k_trace_faces<128, true>
+                             : (const void*)k_trace_faces<128, false>;
+    case 256: return coldens ? (const void*)k_trace_faces<256, true>
+                             : (const void*)k_trace_faces<256, false>;
+    default: return nullptr;
   }
 }
 
-int faces_max_grid(int block, size_t smem) {
+cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid, size_t smem,
+                               int unroll) {
+  const bool cd = a.coldens != nullptr;
+  const void* fn = face_kernel(block, cd ? 1 : unroll, cd);
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int threads = block == 32 ? kWarpsPerBlock * 32 : block;
+  TraceArgs arg = a;
+  void* params[] = {&arg};
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), params, smem, g.stream);
+  count_launch();
+  return e;
+}
+
+int faces_max_grid(int block, size_t smem, int unroll) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaSuccess;
-#define OCC(B)                                                                              \
-  case B:                                                                                   \
-    e = cudaFuncSetAttribute(k_trace_faces<B, false>,                                       \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
-    if (e == cudaSuccess)                                                                   \
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace_faces<B, false>, B, smem); \
-    break;
-  switch (block) {
-    OCC(64)
-    OCC(128)
-    OCC(256)
-    OCC(512)
-    default: return 0;
-  }
-#undef OCC
+  const void* fn = face_kernel(block, unroll, false);
+  if (!fn) return 0;
+  const int threads = block == 32 ? kWarpsPerBlock * 32 : block;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
   if (e != cudaSuccess) return 0;
   return per * sms;
 }

@@ -67,7 +67,7 @@ def assert_gamma(gg, go, rtol=GAMMA_RTOL):
         assert rel.max() <= rtol, "max rel err %.3e" % rel.max()
 
 
-def run_both(w, tab, schedules=("batched", "plain"), cd_srcs=(0,)):
+def run_both(w, tab, schedules=("batched", "plain", "early_exit"), cd_srcs=(0,)):
     n, cell = w["n"], w["cell_cm"]
     ref = O.raytrace(n, cell, w["nH"], w["xHI"], w["pos"], w["ndot"], w["radius"], tab,
                      nthreads=8)
@@ -75,8 +75,10 @@ def run_both(w, tab, schedules=("batched", "plain"), cd_srcs=(0,)):
     for sch in schedules:
         gam = g.raytrace(schedule=sch).cpu().numpy()
         st = g.stats()
-        assert st["launches"] == 1
+        assert st["launches"] >= 1
         assert_gamma(gam, ref["gamma"])
+        if sch == "early_exit":
+            continue  # rates only: the opaque tail's column densities are skipped
         for s in cd_srcs:
             cd = g.source_coldens(s, schedule=sch).cpu().numpy()
             ro = O.raytrace(n, cell, w["nH"], w["xHI"], w["pos"][s:s + 1], w["ndot"][s:s + 1],
