@@ -275,18 +275,29 @@ def main():
         wl = torch.tensor(np.random.default_rng(2311_01492 + 4).standard_normal(n ** 3), **f64)
         g.set_sources(psub, qsub, rsub)
         sv_sub = float(np.sum(4.0 / 3.0 * math.pi * w["radius"][sel] ** 3))
-        fw, bw = [], []
+        fw, bw, bwf = [], [], []
         for rep in range(3):
             flush.fill_(3.0)
             g.raytrace(gamma, schedule="batched")
             fw.append(g.stats()["trace_ms"])
             flush.fill_(4.0)
+            g.set_adjoint_mode(True)
             g.backward(wl)
             bw.append(g.stats()["trace_ms"])
+            flush.fill_(5.0)
+            g.set_adjoint_mode(False)
+            g.backward(wl)
+            bwf.append(g.stats()["trace_ms"])
+        g.set_adjoint_mode(True)
         adjoint = {"sources": k, "source_voxels_paper": sv_sub,
                    "forward_trace_ms": min(fw), "backward_ms": min(bw),
                    "backward_over_forward": min(bw) / min(fw),
-                   "grad_sv_per_s": sv_sub / (min(bw) * 1e-3)}
+                   "grad_sv_per_s": sv_sub / (min(bw) * 1e-3),
+                   "backward_full_recompute_ms": min(bwf),
+                   "full_recompute_over_forward": min(bwf) / min(fw),
+                   "note": "default adjoint stops each item's recompute at its first opaque "
+                           "layer (exact: no gradient flows beyond); full_recompute recomputes "
+                           "every layer"}
         g.set_sources(pos_d, ndot_d, R_d)
 
     # ---------------- end to end through the public API with host buffers

@@ -165,6 +165,12 @@ rt_status rt_iterate(rt_grid_t g, double* d_x, double dt_s, double alpha_H, doub
 rt_status rt_raytrace_backward(rt_grid_t g, const double* d_dL_dgamma, double* d_dL_dlog_nHI,
                                double* d_dL_dlog_ndot);
 
+/* Adjoint recompute mode: with stop_at_opaque != 0 (default) each item's
+ * recompute stops at its first layer whose cells all have tau_out >= 2^E1 (1+2^-40);
+ * every later tau_in is then >= 2^E1, every later rate exactly 0, and no gradient
+ * flows from there, so the result is the same.  0 recomputes every layer. */
+rt_status rt_set_adjoint_mode(rt_grid_t g, int stop_at_opaque);
+
 /* Timing/launch statistics of the last rt_raytrace on this grid (device event
  * time of the trace kernels, launches, source-voxels traced). */
 typedef struct {

@@ -193,6 +193,10 @@ class Grid:
                 "rt_raytrace_backward")
         return dlogn, dlogndot[:self.nsrc]
 
+    def set_adjoint_mode(self, stop_at_opaque=True):
+        L.check(self._lib.rt_set_adjoint_mode(self._h, int(bool(stop_at_opaque))),
+                "rt_set_adjoint_mode")
+
     def set_schedule(self, block_big=128, hsmall=19, unroll=1):
         L.check(self._lib.rt_set_schedule(self._h, int(block_big), int(hsmall), int(unroll)),
                 "rt_set_schedule")

@@ -606,16 +606,42 @@ rt_status rt_raytrace_backward(rt_grid_t h, const double* d_dL_dgamma, double* d
     g.dq_cap = g.nsrc;
   }
   TRY(cudaMemsetAsync(g.dq_merged, 0, g.nsrc * sizeof(double), g.stream));
-  const int hcap = face_hcap(g.max_r2, g.nmax);
+  // items of large sources by 128-thread CTAs, the rest one per warp (as the trace)
+  const int hbig = face_hcap(g.max_r2, g.nmax);
   const int lcap = std::max(1, std::min(isqrt_h(g.max_r2), g.nmax / 2 + 1));
-  const size_t smem = bwd_smem_bytes(hcap, lcap);
-  if (smem > 227 * 1024)
-    return fail(RT_ERR_INVALID, "rt_raytrace_backward: radius too large for the shared-memory layers");
-  const size_t scap = face_stack_cap(g.max_r2, g.nmax);
-  const int maxg = bwd_max_grid(smem);
-  if (maxg <= 0) return fail(RT_ERR_CUDA, "rt_raytrace_backward: no occupancy");
-  const int grid = std::max(1, std::min(24 * g.nsrc, maxg));
-  const size_t need = scap * sizeof(double2) * (size_t)grid;
+  const int n_items = 24 * g.nsrc;
+  int split = n_items, hsm = 0, r2sm = 0;
+  if (g.hsmall > 0 && !g.r2_sorted_h.empty()) {
+    int lo = 0, hi = (int)g.r2_sorted_h.size();
+    while (lo < hi) {
+      const int mid = (lo + hi) / 2;
+      if (face_hcap(g.r2_sorted_h[mid], g.nmax) <= g.hsmall) hi = mid; else lo = mid + 1;
+    }
+    if (lo < (int)g.r2_sorted_h.size()) {
+      split = 24 * lo;
+      hsm = face_hcap(g.r2_sorted_h[lo], g.nmax);
+      r2sm = g.r2_sorted_h[lo];
+    }
+  }
+  size_t smem_c = 0, smem_w = 0, cap_c = 0, cap_w = 0;
+  int grid_c = 0, grid_w = 0;
+  if (split > 0) {
+    smem_c = bwd_smem_bytes(hbig, lcap);
+    if (smem_c > 227 * 1024)
+      return fail(RT_ERR_INVALID, "rt_raytrace_backward: radius too large for the shared-memory layers");
+    cap_c = face_stack_cap(g.max_r2, g.nmax);
+    const int maxg = bwd_max_grid(smem_c, 128);
+    if (maxg <= 0) return fail(RT_ERR_CUDA, "rt_raytrace_backward: no occupancy");
+    grid_c = std::max(1, std::min(split, maxg));
+  }
+  if (split < n_items) {
+    smem_w = bwd_smem_bytes(hsm, lcap) * 8;
+    cap_w = face_stack_cap(r2sm, g.nmax);
+    const int maxg = bwd_max_grid(smem_w, 32);
+    if (maxg <= 0) return fail(RT_ERR_CUDA, "rt_raytrace_backward: no occupancy (warp mode)");
+    grid_w = std::max(1, std::min((n_items - split + 7) / 8, maxg));
+  }
+  const size_t need = (cap_c * (size_t)grid_c + cap_w * (size_t)grid_w * 8) * sizeof(double2);
   if (need > g.bwd_stack_bytes) {
     cudaFree(g.bwd_stack);
     g.bwd_stack = nullptr;
@@ -625,20 +651,41 @@ rt_status rt_raytrace_backward(rt_grid_t h, const double* d_dL_dgamma, double* d
   }
   TraceArgs a = base_args(g);
   a.items = g.items;
-  a.item_begin = 0;
-  a.n_items = 24 * g.nsrc;
-  a.queue = g.queue;
-  a.hcap = hcap;
-  TRY(cudaMemsetAsync(g.queue, 0, sizeof(int), g.stream));
+  TRY(cudaMemsetAsync(g.queue, 0, 2 * sizeof(int), g.stream));
   TRY(cudaEventRecord(g.ev[1], g.stream));
-  TRY(launch_trace_bwd(g, a, d_dL_dgamma, d_dL_dlog_nHI, g.dq_merged, g.bwd_stack, scap, lcap,
-                       grid, smem));
+  g.stats.launches = 0;
+  if (split > 0) {
+    TraceArgs b = a;
+    b.hcap = hbig;
+    b.item_begin = 0;
+    b.n_items = split;
+    b.queue = g.queue;
+    TRY(launch_trace_bwd(g, b, d_dL_dgamma, d_dL_dlog_nHI, g.dq_merged, g.bwd_stack, cap_c, lcap,
+                         grid_c, smem_c, 128, g.bwd_exit != 0));
+    g.stats.launches += 1;
+  }
+  if (split < n_items) {
+    TraceArgs b = a;
+    b.hcap = hsm;
+    b.item_begin = split;
+    b.n_items = n_items;
+    b.queue = g.queue + 1;
+    TRY(launch_trace_bwd(g, b, d_dL_dgamma, d_dL_dlog_nHI, g.dq_merged,
+                         g.bwd_stack + cap_c * (size_t)grid_c, cap_w, lcap, grid_w, smem_w, 32,
+                         g.bwd_exit != 0));
+    g.stats.launches += 1;
+  }
   TRY(cudaEventRecord(g.ev[2], g.stream));
   TRY(launch_dndot_inputs(g, g.dq_merged, d_dL_dlog_ndot));
-  g.stats.launches = 1;
-  g.stats.block = 256;
-  g.stats.grid = grid;
-  g.stats.items = 24 * g.nsrc;
+  g.stats.block = split > 0 ? 128 : 32;
+  g.stats.grid = split > 0 ? grid_c : grid_w;
+  g.stats.items = n_items;
+  return RT_OK;
+}
+
+rt_status rt_set_adjoint_mode(rt_grid_t h, int stop_at_opaque) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_set_adjoint_mode: null grid");
+  reinterpret_cast<Grid*>(h)->bwd_exit = stop_at_opaque ? 1 : 0;
   return RT_OK;
 }
 

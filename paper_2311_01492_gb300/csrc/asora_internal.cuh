@@ -145,6 +145,7 @@ struct Grid {
   size_t bwd_stack_bytes = 0;
   double* dq_merged = nullptr;   // adjoint: dL/dlog Ndot per merged source
   int dq_cap = 0;
+  int bwd_exit = 1;              // adjoint: stop each item's recompute at its first opaque layer
   bool capturing = false;
 
   // stats
@@ -180,10 +181,10 @@ cudaError_t launch_one_minus(const double* x, double* y, int64_t n, const int* s
                              cudaStream_t s);
 size_t face_stack_cap(int r2, int nmax);
 size_t bwd_smem_bytes(int hcap, int lcap);
-int bwd_max_grid(size_t smem);
+int bwd_max_grid(size_t smem, int block);
 cudaError_t launch_trace_bwd(Grid& g, const TraceArgs& t, const double* w, double* dlogn,
                              double* dndot_merged, double2* stack, size_t stack_cap, int lcap,
-                             int grid, size_t smem);
+                             int grid, size_t smem, int block, bool exit);
 cudaError_t launch_dndot_inputs(Grid& g, const double* dmerged, double* out);
 cudaError_t launch_conv_check(const int64_t* unconv, int64_t limit, int* flag, cudaStream_t s);
 

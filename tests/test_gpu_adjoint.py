@@ -47,13 +47,16 @@ def _box(n, seed, xhi_scale, nsrc):
     return nH, xHI, pos, ndot, R, w
 
 
-@pytest.mark.parametrize("spec,xhi_scale", [("grey_exact", 3e-3), ("bb", 3e-3), ("bb", 1e-9)])
-def test_adjoint_matches_oracle_complex_step(spec, xhi_scale):
+@pytest.mark.parametrize("spec,xhi_scale,stop", [("grey_exact", 3e-3, True), ("bb", 3e-3, True),
+                                                  ("bb", 1e-9, True), ("bb", 0.3, True),
+                                                  ("bb", 0.3, False), ("grey_exact", 0.3, True)])
+def test_adjoint_matches_oracle_complex_step(spec, xhi_scale, stop):
     n = 12
     cell = 10 * S.KPC_CM
     nH, xHI, pos, ndot, R, w = _box(n, 41, xhi_scale, 4)
     tab = O.make_table(spec)
     g = gpu_grid(n, cell, nH, xHI, pos, ndot, R, tab)
+    g.set_adjoint_mode(stop)
     dn, dq = g.backward(dev(w))
     dn = dn.cpu().numpy()
     dq = dq.cpu().numpy()
