@@ -39,7 +39,7 @@ static void free_grid(Grid* g) {
   cudaFree(g->boxes_d); cudaFree(g->gtab); cudaFree(g->htab);
   cudaFree(g->dtau); cudaFree(g->dtauT); cudaFree(g->invn);
   cudaFree(g->src); cudaFree(g->ndot); cudaFree(g->r2lim); cudaFree(g->items);
-  cudaFree(g->src_of_input); cudaFree(g->geo); cudaFree(g->queue); cudaFree(g->err);
+  cudaFree(g->src_of_input); cudaFree(g->geo); cudaFree(g->georow); cudaFree(g->queue); cudaFree(g->err);
   cudaFree(g->cube); cudaFree(g->unconv); cudaFree(g->xbuf); cudaFree(g->xavg);
   cudaFree(g->xavg2); cudaFree(g->xhi_int); cudaFree(g->flags); cudaFree(g->counters);
   cudaFree(g->ndot_in); cudaFree(g->bwd_stack); cudaFree(g->dq_merged);
@@ -57,14 +57,19 @@ static void free_grid(Grid* g) {
 static rt_status ensure_geometry(Grid& g, int mmax) {
   if (mmax <= g.geo_mmax) return RT_OK;
   GeoEntry* geo = nullptr;
+  GeoRow* georow = nullptr;
   TRY(cudaMalloc(&geo, geo_count(mmax) * sizeof(GeoEntry)));
-  cudaError_t e = launch_geometry(geo, mmax, g.stream);
+  cudaError_t e = cudaMalloc(&georow, georow_count(mmax) * sizeof(GeoRow));
+  if (e == cudaSuccess) e = launch_geometry(geo, georow, mmax, g.stream);
   if (e != cudaSuccess) {
     cudaFree(geo);
+    cudaFree(georow);
     return cuda_fail(e, "geometry");
   }
   cudaFree(g.geo);
+  cudaFree(g.georow);
   g.geo = geo;
+  g.georow = georow;
   g.geo_mmax = mmax;
   return RT_OK;
 }
@@ -88,6 +93,7 @@ static TraceArgs base_args(Grid& g) {
   a.r2lim = g.r2lim;
   a.queue = g.queue;
   a.geo = g.geo;
+  a.georow = g.georow;
   a.geo_mmax = g.geo_mmax;
   a.tab.g = g.gtab;
   a.tab.h = g.htab;
@@ -161,6 +167,9 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
     g.stats.launches = 1;
     g.stats.items = nsrc_plain;
   } else {
+    if (g.nmax > 1290)
+      return fail(RT_ERR_INVALID, "rt_raytrace: the batched schedule needs boxes of at most "
+                                  "1290^3 cells (32-bit offsets); use RT_SCHED_PLAIN");
     // Batched: items of large sources are traced by whole CTAs, items whose
     // layers fit g.hsmall by single warps (items are in LPT order, so the
     // warp-mode items are a suffix).

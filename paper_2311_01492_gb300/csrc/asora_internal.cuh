@@ -42,6 +42,19 @@ __host__ __device__ inline int64_t geo_index(int m, int lo, int hi) {
 }
 inline int64_t geo_count(int mmax) { return geo_index(mmax + 1, 0, 0); }
 
+// Row-major geometry for the batched trace: entry (m, a1, a2), 0 <= a1, a2 <= m,
+// holds the weights in the cell's own orientation (a = a1/m, b = a2/m):
+//   w1 = (1-a)(1-b), w2 = a(1-b), w3 = (1-a)b, w4 = ab, ds = sqrt(1 + (a1^2+a2^2)/m^2)
+// (bit-identical to the (lo, hi) table's values; consecutive a2 are adjacent).
+struct __align__(16) GeoRow {
+  double w1, w2, w3, w4;
+  double ds, pad;
+};
+__host__ __device__ inline int64_t georow_index(int m, int a1, int a2) {
+  return (int64_t)m * (m + 1) * (2 * m + 1) / 6 - 1 + (int64_t)a1 * (m + 1) + a2;
+}
+inline int64_t georow_count(int mmax) { return georow_index(mmax + 1, 0, 0); }
+
 // Rate tables on the device.
 struct TabDev {
   const double2* g;  // (c0, c1) per segment
@@ -67,6 +80,7 @@ struct TraceArgs {
   int n_items;           // one past the last item of this launch
   int* queue;            // work counter
   const GeoEntry* geo;
+  const GeoRow* georow;
   int geo_mmax;
   TabDev tab;
   double tau_lim;
@@ -123,6 +137,7 @@ struct Grid {
 
   // geometry
   GeoEntry* geo = nullptr;
+  GeoRow* georow = nullptr;
   int geo_mmax = 0;
 
   // scratch
@@ -164,7 +179,7 @@ rt_status cuda_fail(cudaError_t e, const char* what);
 cudaError_t launch_precompute(Grid& g, const int* skip = nullptr);
 cudaError_t launch_zero(double* p, int64_t n, const int* skip, cudaStream_t s);
 cudaError_t launch_validate_fields(Grid& g, const double* nH, const double* xHI);
-cudaError_t launch_geometry(GeoEntry* geo, int mmax, cudaStream_t s);
+cudaError_t launch_geometry(GeoEntry* geo, GeoRow* georow, int mmax, cudaStream_t s);
 cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid, size_t smem,
                                int unroll);
 cudaError_t launch_trace_shells(Grid& g, const TraceArgs& a, int block, int grid);

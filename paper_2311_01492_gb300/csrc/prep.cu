@@ -129,8 +129,30 @@ __global__ void k_geometry(GeoEntry* __restrict__ geo, int mmax) {
   }
 }
 
-cudaError_t launch_geometry(GeoEntry* geo, int mmax, cudaStream_t s) {
+// Row-major entry (m, a1, a2) with the same correctly rounded expressions.
+__global__ void k_geometry_rows(GeoRow* __restrict__ geo, int mmax) {
+  const int m = blockIdx.x + 1;
+  if (m > mmax) return;
+  const int cnt = (m + 1) * (m + 1);
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const int a1 = t / (m + 1), a2 = t - a1 * (m + 1);
+    const double x = (double)a1 / (double)m;
+    const double y = (double)a2 / (double)m;
+    GeoRow e;
+    e.w1 = (1.0 - x) * (1.0 - y);
+    e.w2 = x * (1.0 - y);
+    e.w3 = (1.0 - x) * y;
+    e.w4 = x * y;
+    e.ds = sqrt(1.0 + (double)(a1 * a1 + a2 * a2) / (double)(m * m));
+    e.pad = 0.0;
+    geo[georow_index(m, a1, a2)] = e;
+  }
+}
+
+cudaError_t launch_geometry(GeoEntry* geo, GeoRow* georow, int mmax, cudaStream_t s) {
   if (mmax < 1) return cudaSuccess;
+  k_geometry_rows<<<mmax, 256, 0, s>>>(georow, mmax);
+  count_launch();
   k_geometry<<<mmax, 256, 0, s>>>(geo, mmax);
   count_launch();
   return cudaGetLastError();

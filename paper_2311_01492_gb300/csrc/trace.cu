@@ -93,12 +93,13 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
   //   z faces read dtauT (k,i,j): index = k N^2 + i N + j  (t1 = i, t2 = j)
   //   y faces read dtau  (i,j,k): index = i N^2 + j N + k  (t1 = i, t2 = k)
   //   x faces read dtau  (i,j,k): index = i N^2 + j N + k  (t1 = j, t2 = k)
-  const int64_t NN = (int64_t)N * N;
+  // 32-bit offsets within the box (the batched schedule requires n^3 < 2^31)
+  const int NN = N * N;
   const int c1 = d == 0 ? S.j : S.i;           // source coordinate along t1
   const int c2 = d == 2 ? S.j : S.k;           // source coordinate along t2
   const int cd = d == 0 ? S.i : (d == 1 ? S.j : S.k);
-  const int64_t m1 = d == 0 ? (int64_t)N : (d == 1 ? NN : (int64_t)N);  // stride of t1
-  const int64_t md = d == 0 ? NN : (d == 1 ? (int64_t)N : NN);          // stride of the layer axis
+  const int m1 = d == 1 ? NN : N;              // stride of t1
+  const int md = d == 1 ? N : NN;              // stride of the layer axis
   const double* __restrict__ fld = (d == 2 ? a.dtauT : a.dtau) + B.off;
 
   double* prev = buf0;
@@ -124,27 +125,25 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
     const int total = rowpre[nrows];
     const int W = H + 1, Wp = Hp + 1;
     const int lc = wrapc(cd + sg * m, N);
-    const int64_t lay = (int64_t)lc * md;
+    const int lay = lc * md;
+    const GeoRow* __restrict__ grow = a.georow + georow_index(m, 0, 0);
     const int gbase = (int)geo_index(m, 0, 0);
     bool opaque = true;  // every cell of this thread has tau_out >= the exit bound
     for (int t = gt; t < total; t += GS) {
       const int a1 = rowof[t];
       const int a2 = t - rowpre[a1];
       const int x1 = wrapc(c1 + q1 * a1, N), x2 = wrapc(c2 + q2 * a2, N);
-      const int64_t gidx = lay + x1 * m1 + x2;
+      const int gidx = lay + x1 * m1 + x2;
       const double dtp = __ldg(&fld[gidx]);
-      const int glo = min(a1, a2), ghi = max(a1, a2);
-      const GeoEntry* ge = &a.geo[gbase + ((ghi * (ghi + 1)) >> 1) + glo];
-      const double2 wv0 = __ldg(reinterpret_cast<const double2*>(ge));      // w1, wa
-      const double2 wv1 = __ldg(reinterpret_cast<const double2*>(ge) + 1);  // wb, w4
-      const double ds = __ldg(&ge->ds);
+      const GeoRow* gr = grow + a1 * (m + 1) + a2;
+      const double2 wv0 = __ldg(reinterpret_cast<const double2*>(gr));      // w1, w2
+      const double2 wv1 = __ldg(reinterpret_cast<const double2*>(gr) + 1);  // w3, w4
+      const double ds = __ldg(&gr->ds);
       double tin;
       if (m == 1) {
         tin = (0.5 * dts) * ds;
       } else {
-        const double w1 = wv0.x, w4 = wv1.y;
-        const double w2 = a1 <= a2 ? wv0.y : wv1.x;
-        const double w3 = a1 <= a2 ? wv1.x : wv0.y;
+        const double w1 = wv0.x, w2 = wv0.y, w3 = wv1.x, w4 = wv1.y;
         const int b1 = min(a1, Hp), b2 = min(a1 - (a1 > 0), Hp);
         const int e1 = min(a2, Hp), e2 = min(a2 - (a2 > 0), Hp);
         const double v1 = prev[b1 * Wp + e1];
@@ -161,10 +160,11 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
       if (!own) continue;
       if (COLDENS || bits_of(tin) < a.tab.tau_max_bits) {
         // C-order index of the cell (the z faces gathered from the rotated copy)
-        const int64_t cell = B.off + (d == 2 ? ((int64_t)x1 * N + x2) * N + lc : gidx);
+        const int64_t cell = B.off + (d == 2 ? (x1 * N + x2) * N + lc : gidx);
         if (COLDENS) {
           a.coldens[cell] = tout / a.sigma0;
         } else {
+          const GeoEntry* ge = &a.geo[gbase + ((max(a1, a2) * (max(a1, a2) + 1)) >> 1) + min(a1, a2)];
           const double dcell = dtp * ds;
           const double dG = cell_rate(a, nd, tin, tout, dcell, __ldg(&ge->invv) * B.inv_cell3,
                                       __ldg(&ge->thin) * B.thin_fac,
