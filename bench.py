@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=1, help="timed RT_SCHED_PLAIN traces")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default batched schedule instead of timing candidates")
+    ap.add_argument("--block", type=int, default=128, choices=(128, 256),
+                    help="with --no-autotune: threads per CTA of the large-source kernel")
+    ap.add_argument("--hsmall", type=int, default=19,
+                    help="with --no-autotune: largest layer half-width traced by single warps")
     ap.add_argument("--adjoint-src", type=int, default=100_000,
                     help="sources of the gradient-throughput measurement (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -230,7 +234,8 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     g.set_sources(pos_d, ndot_d, R_d)
     if args.no_autotune:
-        tuned = (128, 19)
+        tuned = (args.block, args.hsmall)
+        g.set_schedule(*tuned)
     else:
         tuned = g.autotune(os.path.join(ROOT, "gpurun_out", "autotune_cache.txt")
                            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)

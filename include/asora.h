@@ -189,12 +189,12 @@ typedef struct {
 
 /* Schedule of RT_SCHED_BATCHED: items of sources whose largest layer half-width
  * exceeds hsmall are traced by CTAs of block_big threads (128 or 256), the
- * others by single warps (hsmall 0..24; 0 = CTAs only); unroll must be 1.
- * Defaults 128, 19, 1; results do not depend on the choice. */
-rt_status rt_set_schedule(rt_grid_t g, int block_big, int hsmall, int unroll);
+ * others by single warps (hsmall 0..32; 0 = CTAs only).  Defaults 128, 19;
+ * results do not depend on the choice. */
+rt_status rt_set_schedule(rt_grid_t g, int block_big, int hsmall);
 
 /* Autotuner of RT_SCHED_BATCHED: times rt_raytrace on the registered fields and
- * sources for block_big in {128, 256} and hsmall in {0, 11, 15, 19, 22}, keeps the
+ * sources for block_big in {128, 256} and hsmall in {0, 11, 15, 19, 22, 24, 27}, keeps the
  * fastest and returns it in *h_block, *h_hsmall (either may be NULL).  With a
  * cache file (may be NULL), a line "<workload key> <block> <hsmall>" whose key
  * (box sizes, source count and radius distribution) matches is used without

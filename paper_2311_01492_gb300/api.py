@@ -197,8 +197,8 @@ class Grid:
         L.check(self._lib.rt_set_adjoint_mode(self._h, int(bool(stop_at_opaque))),
                 "rt_set_adjoint_mode")
 
-    def set_schedule(self, block_big=128, hsmall=19, unroll=1):
-        L.check(self._lib.rt_set_schedule(self._h, int(block_big), int(hsmall), int(unroll)),
+    def set_schedule(self, block_big=128, hsmall=19):
+        L.check(self._lib.rt_set_schedule(self._h, int(block_big), int(hsmall)),
                 "rt_set_schedule")
 
     def autotune(self, cache_path=None):

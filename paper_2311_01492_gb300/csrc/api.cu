@@ -195,7 +195,7 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
       if (smem > 227 * 1024)
         return fail(RT_ERR_INVALID, "rt_raytrace: radius too large for the batched schedule's "
                                     "shared-memory layers; use RT_SCHED_PLAIN");
-      const int maxg = faces_max_grid(block, smem, g.unroll);
+      const int maxg = faces_max_grid(block, smem);
       if (maxg <= 0) return fail(RT_ERR_CUDA, "rt_raytrace: no occupancy for the face kernel");
       TraceArgs b = a;
       b.hcap = hbig;
@@ -203,14 +203,14 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
       b.n_items = split;
       b.queue = g.queue;
       const int grid = std::max(1, std::min(split, maxg));
-      TRY(launch_trace_faces(g, b, block, grid, smem, g.unroll));
+      TRY(launch_trace_faces(g, b, block, grid, smem));
       g.stats.block = block;
       g.stats.grid = grid;
       g.stats.launches += 1;
     }
     if (split < n_items) {
       const size_t smem = faces_smem_bytes(hsm, 32) * g.warps_per_block;
-      const int maxg = faces_max_grid(32, smem, g.unroll);
+      const int maxg = faces_max_grid(32, smem);
       if (maxg <= 0) return fail(RT_ERR_CUDA, "rt_raytrace: no occupancy for the warp face kernel");
       TraceArgs b = a;
       b.hcap = hsm;
@@ -219,7 +219,7 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
       b.queue = g.queue + 1;
       const int nitem = n_items - split;
       const int grid = std::max(1, std::min((nitem + g.warps_per_block - 1) / g.warps_per_block, maxg));
-      TRY(launch_trace_faces(g, b, 32, grid, smem, g.unroll));
+      TRY(launch_trace_faces(g, b, 32, grid, smem));
       g.stats.launches += 1;
       if (split == 0) {
         g.stats.block = 32;
@@ -698,17 +698,15 @@ rt_status rt_set_adjoint_mode(rt_grid_t h, int stop_at_opaque) {
   return RT_OK;
 }
 
-rt_status rt_set_schedule(rt_grid_t h, int block_big, int hsmall, int unroll) {
+rt_status rt_set_schedule(rt_grid_t h, int block_big, int hsmall) {
   if (!h) return fail(RT_ERR_INVALID, "rt_set_schedule: null grid");
   if (block_big != 128 && block_big != 256)
     return fail(RT_ERR_INVALID, "rt_set_schedule: block must be 128 or 256");
-  if (unroll != 1) return fail(RT_ERR_INVALID, "rt_set_schedule: unroll must be 1");
-  if (hsmall < 0 || hsmall > 24)
-    return fail(RT_ERR_INVALID, "rt_set_schedule: hsmall must be 0..24");
+  if (hsmall < 0 || hsmall > 32)
+    return fail(RT_ERR_INVALID, "rt_set_schedule: hsmall must be 0..32");
   Grid& g = *reinterpret_cast<Grid*>(h);
   g.block_big = block_big;
   g.hsmall = hsmall;
-  g.unroll = unroll;
   return RT_OK;
 }
 
@@ -736,7 +734,7 @@ rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_
       std::istringstream ls(line);
       std::string k;
       int b = 0, hs = -1;
-      if ((ls >> k >> b >> hs) && k == key && (b == 128 || b == 256) && hs >= 0 && hs <= 24) {
+      if ((ls >> k >> b >> hs) && k == key && (b == 128 || b == 256) && hs >= 0 && hs <= 32) {
         g.block_big = b;
         g.hsmall = hs;
         if (h_block) *h_block = b;
@@ -749,7 +747,7 @@ rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_
   double* gam = nullptr;
   TRY(cudaMalloc(&gam, g.ncell * sizeof(double)));
   const int blocks[] = {128, 256};
-  const int hss[] = {0, 11, 15, 19, 22};
+  const int hss[] = {0, 11, 15, 19, 22, 24, 27};
   float best = 1e30f;
   int bb = g.block_big, bh = g.hsmall;
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -67,14 +67,15 @@ __device__ __forceinline__ double tab_slope(const double2* __restrict__ t, const
   return __ldg(&t[seg]).y;
 }
 
-// Shared memory of one group (a CTA, or one warp in warp mode) tracing a
-// quadrant of a face with layer half-width capacity h: two layers of (h+1)^2
-// doubles, and two sets of row tables (the current layer's and the next's):
-// first flat index of every row (h+2 ints) and the row of every flat index
-// (bytes; rows < 256 since h <= 254).
-__host__ __device__ inline size_t group_smem_bytes(int h) {
+// Shared memory of one group tracing a quadrant of a face with layer half-width
+// capacity h: two layers of (h+1)^2 doubles in CTA mode, one (updated in place)
+// in warp mode, and two sets of row tables (the current layer's and the
+// next's): first flat index of every row (h+2 ints) and the row of every flat
+// index (bytes; rows < 256 since h <= 254).
+__host__ __device__ inline size_t group_smem_bytes(int h, bool warp) {
   const size_t cap = (size_t)(h + 1) * (h + 1);
-  const size_t b = 2 * cap * sizeof(double) + 2 * (size_t)(h + 2) * sizeof(int) + 2 * cap;
+  const size_t b = (warp ? 1 : 2) * cap * sizeof(double) + 2 * (size_t)(h + 2) * sizeof(int) +
+                   2 * cap;
   return (b + 15) & ~(size_t)15;
 }
 

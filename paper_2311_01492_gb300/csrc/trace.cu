@@ -37,9 +37,7 @@
 namespace asora {
 
 // ----------------------------------------------------------- face kernels
-size_t faces_smem_bytes(int hcap, int block) {
-  return block == 32 ? group_smem_bytes(hcap) : group_smem_bytes(hcap);
-}
+size_t faces_smem_bytes(int hcap, int block) { return group_smem_bytes(hcap, block == 32); }
 
 // Trace one (source, face, quadrant) item with a group of GS threads (gt =
 // thread index in the group).  Within a face, a cell's interpolants never
@@ -47,14 +45,22 @@ size_t faces_smem_bytes(int hcap, int block) {
 // (sign of t1, sign of t2, the lines included) depends only on itself; the
 // lines are traced by both neighbouring quadrants and owned by the + side.
 // Layers m = 1..Lmax; every cell reads only layer m-1.
+//
+// CTA mode (GS > 32) keeps layer m-1 and layer m in two buffers.  Warp mode
+// (GS == 32) keeps one buffer with a fixed row stride and updates it in place:
+// the cells are taken in descending flat order, 32 at a time, and every lane
+// reads its interpolants before any lane writes.  A cell reads only slots
+// (b <= a1, e <= a2), whose flat index in the current layer is not above its
+// own, so each such slot is rewritten in the same round (after the reads) or in
+// a later round -- never before it is read.
 template <int GS, bool COLDENS>
 __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int item, const int gt,
                                                 unsigned char* __restrict__ sm, const int h,
                                                 unsigned& nrate) {
   const int cap = (h + 1) * (h + 1);
   double* buf0 = reinterpret_cast<double*>(sm);
-  double* buf1 = buf0 + cap;
-  int* rowpre2 = reinterpret_cast<int*>(buf1 + cap);                       // [2][h+2]
+  double* buf1 = GS == 32 ? buf0 : buf0 + cap;
+  int* rowpre2 = reinterpret_cast<int*>(buf0 + (GS == 32 ? 1 : 2) * cap);  // [2][h+2]
   unsigned char* rowof2 = reinterpret_cast<unsigned char*>(rowpre2 + 2 * (h + 2));  // [2][cap]
   const int wid = gt >> 5, lane = gt & 31;
 
@@ -123,13 +129,17 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
     const int* rowpre = rowpre2 + (m & 1) * (h + 2);
     const unsigned char* rowof = rowof2 + (m & 1) * cap;
     const int total = rowpre[nrows];
-    const int W = H + 1, Wp = Hp + 1;
+    const int W = GS == 32 ? h + 1 : H + 1, Wp = GS == 32 ? h + 1 : Hp + 1;
     const int lc = wrapc(cd + sg * m, N);
     const int lay = lc * md;
     const GeoRow* __restrict__ grow = a.georow + georow_index(m, 0, 0);
     const int gbase = (int)geo_index(m, 0, 0);
     bool opaque = true;  // every cell of this thread has tau_out >= the exit bound
-    for (int t = gt; t < total; t += GS) {
+    for (int t0 = GS == 32 ? total - 1 : gt; GS == 32 ? t0 >= 0 : t0 < total;
+         t0 += GS == 32 ? -32 : GS) {
+      // warp mode: lanes take t0, t0-1, ..., t0-31; lanes below 0 recompute cell 0
+      // and write nothing
+      const int t = GS == 32 ? max(t0 - lane, 0) : t0;
       const int a1 = rowof[t];
       const int a2 = t - rowpre[a1];
       const int x1 = wrapc(c1 + q1 * a1, N), x2 = wrapc(c2 + q2 * a2, N);
@@ -153,6 +163,10 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
         tin = fma(w4, v4, fma(w3, v3, fma(w2, v2, w1 * v1)));
       }
       const double tout = fma(dtp, ds, tin);
+      if (GS == 32) {
+        __syncwarp();  // every lane has read layer m-1 before any lane writes
+        if (t0 - lane < 0) continue;
+      }
       cur[a1 * W + a2] = tout;
       opaque = opaque && bits_of(tout) >= a.exit_bits;
       const bool own = ((d == 2) || (d == 1 ? a2 < m : (a1 < m && a2 < m))) &&
@@ -237,10 +251,10 @@ __global__ void __launch_bounds__(WPB * 32, 1024 / (WPB * 32)) k_trace_faces_war
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (a.skip && *a.skip) return;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* my = smem_raw + (size_t)wid * group_smem_bytes(a.hcap);
+  unsigned char* my = smem_raw + (size_t)wid * group_smem_bytes(a.hcap, true);
   const int cap = (a.hcap + 1) * (a.hcap + 1);
   double* buf = reinterpret_cast<double*>(my);
-  for (int t = lane; t < 2 * cap; t += 32) buf[t] = 0.0;
+  for (int t = lane; t < cap; t += 32) buf[t] = 0.0;  // one layer buffer per warp
   __syncwarp();
   unsigned nrate = 0;
   for (;;) {
@@ -258,7 +272,7 @@ constexpr int kWarpsPerBlock = 8;
 
 // Kernel variant for (block, coldens); block 32 = warp mode.  Null if not
 // instantiated.
-static const void* face_kernel(int block, int /*unroll*/, bool coldens) {
+static const void* face_kernel(int block, bool coldens) {
   switch (block) {
     case 32: return coldens ? (const void*)k_trace_faces_warp<kWarpsPerBlock, true>
                             : (const void*)k_trace_faces_warp<kWarpsPerBlock, false>;
@@ -270,10 +284,9 @@ static const void* face_kernel(int block, int /*unroll*/, bool coldens) {
   }
 }
 
-cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid, size_t smem,
-                               int unroll) {
+cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid, size_t smem) {
   const bool cd = a.coldens != nullptr;
-  const void* fn = face_kernel(block, cd ? 1 : unroll, cd);
+  const void* fn = face_kernel(block, cd);
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -285,11 +298,11 @@ cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid,
   return e;
 }
 
-int faces_max_grid(int block, size_t smem, int unroll) {
+int faces_max_grid(int block, size_t smem) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const void* fn = face_kernel(block, unroll, false);
+  const void* fn = face_kernel(block, false);
   if (!fn) return 0;
   const int threads = block == 32 ? kWarpsPerBlock * 32 : block;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -67,11 +67,13 @@ def assert_gamma(gg, go, rtol=GAMMA_RTOL):
         assert rel.max() <= rtol, "max rel err %.3e" % rel.max()
 
 
-def run_both(w, tab, schedules=("batched", "plain", "early_exit"), cd_srcs=(0,)):
+def run_both(w, tab, schedules=("batched", "plain", "early_exit"), cd_srcs=(0,), sched=None):
     n, cell = w["n"], w["cell_cm"]
     ref = O.raytrace(n, cell, w["nH"], w["xHI"], w["pos"], w["ndot"], w["radius"], tab,
                      nthreads=8)
     g = make_gpu(n, cell, w["nH"], w["xHI"], w["pos"], w["ndot"], w["radius"], tab)
+    if sched is not None:
+        g.set_schedule(*sched)
     for sch in schedules:
         gam = g.raytrace(schedule=sch).cpu().numpy()
         st = g.stats()
@@ -126,6 +128,29 @@ def _random_box(n, nsrc, rmax, seed, dup=True):
                                               (24, 60, 12.0, 3), (9, 5, 40.0, 4)])
 def test_lognormal_boxes_many_sources(n, nsrc, rmax, seed):
     run_both(_random_box(n, nsrc, rmax, seed), table("bb"), cd_srcs=(0, 1, 3))
+
+
+# batched launch configurations (block_big, hsmall): CTAs only (hsmall 0), mixes
+# of CTA and warp items, and warps for every item that fits
+SCHEDS = [(128, 0), (256, 0), (128, 11), (256, 19), (128, 24)]
+
+
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_every_batched_configuration(sched):
+    """Same column densities (bit for bit) and rates in every CTA/warp configuration,
+    including windows that clip the faces (even, odd and tiny boxes)."""
+    for n, nsrc, rmax, seed in [(16, 20, 12.0, 1), (17, 30, 25.0, 2), (24, 40, 12.0, 3),
+                                (9, 5, 40.0, 4)]:
+        run_both(_random_box(n, nsrc, rmax, seed), table("bb"), schedules=("batched", "early_exit"),
+                 cd_srcs=(0, 1, 3), sched=sched)
+    run_both(S.single_source_uniform(), table("bb"), schedules=("batched",), sched=sched)
+    run_both(S.single_source_uniform(xhi=1e-12, radius=15.0), table("grey_exact"),
+             schedules=("batched",), sched=sched)
+    for n, R in [(1, 5.0), (2, 3.0), (8, 100.0)]:
+        w = dict(n=n, cell_cm=10 * S.KPC_CM, nH=np.full((n, n, n), 1e-3),
+                 xHI=np.full((n, n, n), 1e-4), pos=np.zeros((1, 3), np.int32),
+                 ndot=np.array([1e50]), radius=np.array([R]))
+        run_both(w, table("bb"), schedules=("batched",), sched=sched)
 
 
 def test_degenerate_sizes():
