@@ -185,6 +185,7 @@ typedef struct {
   int schedule;             /* schedule used                                        */
   int block;                /* threads per CTA of the trace kernel                  */
   int grid;                 /* CTAs of the trace kernel                             */
+  int64_t row_table_bytes;  /* precomputed row tables of the ingested radii (0: none) */
 } rt_stats;
 
 /* Schedule of RT_SCHED_BATCHED: items of sources whose largest layer half-width

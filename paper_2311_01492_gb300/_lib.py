@@ -26,7 +26,8 @@ class rt_stats(C.Structure):
     _fields_ = [("trace_ms", C.c_double), ("prep_ms", C.c_double),
                 ("source_voxels", C.c_int64), ("items", C.c_int64), ("rate_cells", C.c_int64),
                 ("kernel_launches", C.c_int64), ("launches", C.c_int),
-                ("schedule", C.c_int), ("block", C.c_int), ("grid", C.c_int)]
+                ("schedule", C.c_int), ("block", C.c_int), ("grid", C.c_int),
+                ("row_table_bytes", C.c_int64)]
 
 
 _L = None

@@ -43,6 +43,7 @@ static void free_grid(Grid* g) {
   cudaFree(g->cube); cudaFree(g->unconv); cudaFree(g->xbuf); cudaFree(g->xavg);
   cudaFree(g->xavg2); cudaFree(g->xhi_int); cudaFree(g->flags); cudaFree(g->counters);
   cudaFree(g->ndot_in); cudaFree(g->bwd_stack); cudaFree(g->dq_merged);
+  free_row_tables(*g);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
   delete g;
@@ -94,6 +95,12 @@ static TraceArgs base_args(Grid& g) {
   a.queue = g.queue;
   a.geo = g.geo;
   a.georow = g.georow;
+  a.rtab = g.rtab;
+  a.rtab_off = g.rtab_off;
+  a.rtab_first = g.rtab_first;
+  a.rtab_hcap = g.rtab_hcap;
+  a.rtab_slot = g.rtab_slot;
+  a.rtab_max_r2 = g.rtab_max_r2;
   a.geo_mmax = g.geo_mmax;
   a.tab.g = g.gtab;
   a.tab.h = g.htab;
@@ -402,7 +409,9 @@ rt_status rt_set_sources(rt_grid_t h, int nsrc, const int32_t* d_pos, const int3
   rt_status st = ingest_sources(g, nsrc, d_pos, d_box, d_ndot, d_radius);
   if (st != RT_OK) return st;
   const int mmax = std::max(1, std::min(isqrt_h(g.max_r2), g.nmax / 2 + 1));
-  return ensure_geometry(g, mmax);
+  st = ensure_geometry(g, mmax);
+  if (st != RT_OK) return st;
+  return ensure_row_tables(g);
 }
 
 rt_status rt_raytrace(rt_grid_t h, double* d_gamma, int schedule) {
@@ -474,6 +483,7 @@ rt_status rt_get_stats(rt_grid_t h, rt_stats* out) {
   TRY(cudaMemcpy(&rc, g.counters, sizeof(rc), cudaMemcpyDeviceToHost));
   g.stats.rate_cells = (int64_t)rc;
   g.stats.kernel_launches = g_launches.load();
+  g.stats.row_table_bytes = g.rtab ? g.rtab_bytes : 0;
   *out = g.stats;
   int herr = 0;
   TRY(cudaMemcpy(&herr, g.err, sizeof(int), cudaMemcpyDeviceToHost));

@@ -92,6 +92,16 @@ struct TraceArgs {
   unsigned long long* rate_cells;  // number of rate evaluations (may be null)
   int early_exit;        // stop an item once a whole layer is opaque (rates only)
   uint64_t exit_bits;    // bits of the opacity bound 2^E1 (1 + 2^-40)
+  // Row tables of unclipped quadrant layers, one blob per (R^2 limit, m):
+  // first flat index of rows 0..H+1 (ints) then the row of every flat index
+  // (bytes), padded to 16 bytes.  Blob of layer m of an item with limit r2:
+  // rtab + rtab_off[rtab_first[rtab_slot[r2]] + m - 1] (rtab_slot[r2] < 0: none).
+  const unsigned char* rtab;
+  const int* rtab_off;    // byte offset of every blob, plus one past the last
+  const int* rtab_first;  // first blob of each R^2 limit
+  const int* rtab_hcap;   // largest layer half-width of each R^2 limit
+  const int* rtab_slot;   // R^2 limit -> slot, for 0..rtab_max_r2
+  int rtab_max_r2;        // -1: no tables
 };
 
 enum ErrBits { ERR_LAYER_CAP = 1, ERR_GEO = 2, ERR_INPUT = 4, ERR_CUBE = 8 };
@@ -135,6 +145,17 @@ struct Grid {
   int64_t source_voxels = 0;
   std::vector<int> r2_sorted_h;  // per merged source (LPT order), host copy
 
+  // precomputed row tables of the batched trace (see TraceArgs::rtab)
+  unsigned char* rtab = nullptr;
+  int* rtab_off = nullptr;
+  int* rtab_first = nullptr;
+  int* rtab_hcap = nullptr;
+  int* rtab_slot = nullptr;
+  int rtab_max_r2 = -1;
+  int rtab_mcap = 0;
+  int64_t rtab_bytes = 0;
+  std::vector<int> rtab_r2s;  // the R^2 limits the tables were built for (descending)
+
   // geometry
   GeoEntry* geo = nullptr;
   GeoRow* georow = nullptr;
@@ -169,6 +190,11 @@ struct Grid {
 
 // Kernels launched by this library in this process (host-side count).
 void count_launch(int n = 1);
+
+// Row tables for the distinct R^2 limits of the ingested sources (prep.cu);
+// kept while the set of limits and the window size do not change.
+rt_status ensure_row_tables(Grid& g);
+void free_row_tables(Grid& g);
 
 // error reporting (api.cu)
 rt_status fail(rt_status st, const std::string& msg);

@@ -67,16 +67,41 @@ __device__ __forceinline__ double tab_slope(const double2* __restrict__ t, const
   return __ldg(&t[seg]).y;
 }
 
+// Row tables of one quadrant layer in shared memory (one slot): the first flat
+// index of rows 0..nrows (nrows+1 ints) followed by the row of every flat index
+// (bytes; rows < 256 since h <= 254), the same layout as the precomputed blobs;
+// a slot holds any layer of half-width <= h.
+__host__ __device__ inline int row_slot_bytes(int h) {
+  return (4 * (h + 2) + (h + 1) * (h + 1) + 15) & ~15;
+}
+
 // Shared memory of one group tracing a quadrant of a face with layer half-width
 // capacity h: two layers of (h+1)^2 doubles in CTA mode, one (updated in place)
-// in warp mode, and two sets of row tables (the current layer's and the
-// next's): first flat index of every row (h+2 ints) and the row of every flat
-// index (bytes; rows < 256 since h <= 254).
-__host__ __device__ inline size_t group_smem_bytes(int h, bool warp) {
+// in warp mode, then (16-byte aligned, for cp.async) two row-table slots: the
+// current layer's and the next's.
+__host__ __device__ inline size_t layer_bytes(int h, bool warp) {
   const size_t cap = (size_t)(h + 1) * (h + 1);
-  const size_t b = (warp ? 1 : 2) * cap * sizeof(double) + 2 * (size_t)(h + 2) * sizeof(int) +
-                   2 * cap;
-  return (b + 15) & ~(size_t)15;
+  return ((warp ? 1 : 2) * cap * sizeof(double) + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t group_smem_bytes(int h, bool warp) {
+  return layer_bytes(h, warp) + 2 * (size_t)row_slot_bytes(h);
+}
+
+// Asynchronous copy of a precomputed row-table blob (16-byte aligned, size a
+// multiple of 16) into a shared-memory slot by the GS threads of a group; the
+// copies complete at the next cp_async_wait_all of each issuing thread.
+template <int GS>
+__device__ __forceinline__ void stage_rows(const unsigned char* __restrict__ src, int bytes,
+                                           unsigned char* dst, int gt) {
+  for (int c = gt * 16; c < bytes; c += GS * 16) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst + c);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src + c) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 template <int GS>

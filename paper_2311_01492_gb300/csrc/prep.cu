@@ -373,13 +373,17 @@ rt_status ingest_sources(Grid& g, int nsrc, const int32_t* d_pos, const int32_t*
     CK(cudaMemcpyAsync(sh.data(), g.src, nm * sizeof(SrcDev), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     std::map<std::pair<int, int>, int64_t> memo;
-    int64_t sv = 0;
-    for (int p = 0; p < nm; ++p) {
-      const int n = g.boxes_h[sh[p].box].n;
-      auto key = std::make_pair(g.r2_sorted_h[p], n);
-      auto it = memo.find(key);
-      if (it == memo.end()) it = memo.emplace(key, ball_count(key.first, n)).first;
-      sv += it->second;
+    int64_t sv = 0, last_cnt = 0;
+    std::pair<int, int> last_key(-1, -1);
+    for (int p = 0; p < nm; ++p) {  // sources come sorted by r2: runs of equal keys
+      const auto key = std::make_pair(g.r2_sorted_h[p], g.boxes_h[sh[p].box].n);
+      if (key != last_key) {
+        auto it = memo.find(key);
+        if (it == memo.end()) it = memo.emplace(key, ball_count(key.first, key.second)).first;
+        last_key = key;
+        last_cnt = it->second;
+      }
+      sv += last_cnt;
     }
     g.source_voxels = sv;
   }
@@ -391,6 +395,161 @@ done:
   cudaFree(lkey); cudaFree(lkey2); cudaFree(lval); cudaFree(order); cudaFree(lpt_of_merged);
   cudaFree(tmp);
   return st;
+}
+
+// ------------------------------------------------------------ row tables
+// Row tables of the unclipped quadrant layers of every distinct R^2 limit: the
+// batched trace stages them into shared memory instead of building them per
+// item (all 24 items of a source, and all sources with the same limit, share
+// them).  Blob of (r2, m): rowpre[0..H+1] (ints: first flat index of row a1,
+// then the layer size) and rowof[0..total) (bytes: row of every flat index),
+// with H = min(m, isqrt(r2 - m^2)) and row a1 holding a2 = 0..min(H,
+// isqrt(r2 - m^2 - a1^2)).
+static int isqrt_host(int64_t x) {
+  if (x < 0) return -1;
+  int r = (int)std::sqrt((double)x);
+  while ((int64_t)r * r > x) --r;
+  while ((int64_t)(r + 1) * (r + 1) <= x) ++r;
+  return r;
+}
+
+__global__ void k_row_tables(const int* __restrict__ ent_r2, const int* __restrict__ ent_m,
+                             const int* __restrict__ off, unsigned char* __restrict__ rtab,
+                             int nent) {
+  const int e = blockIdx.x;
+  if (e >= nent) return;
+  const int m = ent_m[e];
+  const int rem = ent_r2[e] - m * m;
+  int H = (int)sqrtf((float)rem);
+  while (H * H > rem) --H;
+  while ((H + 1) * (H + 1) <= rem) ++H;
+  H = min(H, m);
+  const int nrows = H + 1;
+  int* rowpre = reinterpret_cast<int*>(rtab + off[e]);
+  unsigned char* rowof = reinterpret_cast<unsigned char*>(rowpre + nrows + 1);
+  __shared__ int pre[256 + 1];
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int r = 0; r < nrows; ++r) {
+      pre[r] = run;
+      const int x = rem - r * r;
+      int w = (int)sqrtf((float)x);
+      while (w * w > x) --w;
+      while ((w + 1) * (w + 1) <= x) ++w;
+      run += min(H, w) + 1;
+    }
+    pre[nrows] = run;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r <= nrows; r += blockDim.x) rowpre[r] = pre[r];
+  for (int r = 0; r < nrows; ++r)
+    for (int c = pre[r] + threadIdx.x; c < pre[r + 1]; c += blockDim.x) rowof[c] = (unsigned char)r;
+  // zero the padding up to the next 16-byte boundary
+  const int used = 4 * (nrows + 1) + pre[nrows];
+  for (int b = used + threadIdx.x; b < off[e + 1] - off[e]; b += blockDim.x)
+    rtab[off[e] + b] = 0;
+}
+
+void free_row_tables(Grid& g) {
+  cudaFree(g.rtab); cudaFree(g.rtab_off); cudaFree(g.rtab_first); cudaFree(g.rtab_hcap);
+  cudaFree(g.rtab_slot);
+  g.rtab = nullptr; g.rtab_off = g.rtab_first = g.rtab_hcap = g.rtab_slot = nullptr;
+  g.rtab_max_r2 = -1;
+  g.rtab_bytes = 0;
+  g.rtab_r2s.clear();
+  g.rtab_mcap = 0;
+}
+
+rt_status ensure_row_tables(Grid& g) {
+  rt_status st = RT_OK;
+  // distinct limits, descending (r2_sorted_h is in LPT order: descending)
+  std::vector<int> r2s;
+  for (int v : g.r2_sorted_h)
+    if (r2s.empty() || v != r2s.back()) r2s.push_back(v);
+  std::sort(r2s.begin(), r2s.end(), std::greater<int>());
+  r2s.erase(std::unique(r2s.begin(), r2s.end()), r2s.end());
+  const int mcap = g.nmax / 2 + 1;  // no window has more layers
+  if (r2s == g.rtab_r2s && mcap == g.rtab_mcap && (g.rtab || r2s.empty())) return RT_OK;
+  free_row_tables(g);
+  if (r2s.empty()) {
+    g.rtab_mcap = mcap;
+    return RT_OK;
+  }
+  std::vector<int> ent_r2, ent_m, off, first(r2s.size()), hcap(r2s.size());
+  int64_t cur = 0;
+  for (size_t i = 0; i < r2s.size(); ++i) {
+    const int v = r2s[i];
+    const int L = std::min(isqrt_host(v), mcap);
+    first[i] = (int)ent_m.size();
+    int hc = 0;
+    for (int m = 1; m <= L; ++m) {
+      const int64_t rem = (int64_t)v - (int64_t)m * m;
+      const int H = std::min(m, isqrt_host(rem));
+      int64_t total = 0;
+      for (int r = 0; r <= H; ++r) total += std::min(H, isqrt_host(rem - (int64_t)r * r)) + 1;
+      hc = std::max(hc, H);
+      ent_r2.push_back(v);
+      ent_m.push_back(m);
+      off.push_back((int)cur);
+      cur += (4 * (int64_t)(H + 2) + total + 15) & ~(int64_t)15;
+      if (cur > (int64_t)1 << 30 || H > 254) {  // keep offsets in int, rows in bytes
+        g.rtab_r2s = r2s;
+        g.rtab_mcap = mcap;
+        return RT_OK;  // no tables: the trace builds its own
+      }
+    }
+    hcap[i] = hc;
+  }
+  off.push_back((int)cur);
+  const int nent = (int)ent_m.size();
+  const int maxv = r2s.front();
+  std::vector<int> slot(maxv + 1, -1);
+  for (size_t i = 0; i < r2s.size(); ++i) slot[r2s[i]] = (int)i;
+  int *d_r2 = nullptr, *d_m = nullptr;
+  cudaStream_t s = g.stream;
+#undef CK
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) {                    \
+      st = cuda_fail(e_, #x);                   \
+      goto fail;                                \
+    }                                           \
+  } while (0)
+  CK(cudaMalloc(&g.rtab, std::max<int64_t>(cur, 16)));
+  CK(cudaMalloc(&g.rtab_off, off.size() * sizeof(int)));
+  CK(cudaMalloc(&g.rtab_first, first.size() * sizeof(int)));
+  CK(cudaMalloc(&g.rtab_hcap, hcap.size() * sizeof(int)));
+  CK(cudaMalloc(&g.rtab_slot, slot.size() * sizeof(int)));
+  CK(cudaMalloc(&d_r2, std::max(nent, 1) * sizeof(int)));
+  CK(cudaMalloc(&d_m, std::max(nent, 1) * sizeof(int)));
+  CK(cudaMemcpyAsync(g.rtab_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(g.rtab_first, first.data(), first.size() * sizeof(int),
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(g.rtab_hcap, hcap.data(), hcap.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(g.rtab_slot, slot.data(), slot.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_r2, ent_r2.data(), nent * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_m, ent_m.data(), nent * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (nent > 0) {
+    k_row_tables<<<nent, 64, 0, s>>>(d_r2, d_m, g.rtab_off, g.rtab, nent);
+    count_launch();
+    CK(cudaGetLastError());
+  }
+  CK(cudaStreamSynchronize(s));  // host vectors go out of scope
+  cudaFree(d_r2);
+  cudaFree(d_m);
+  g.rtab_max_r2 = maxv;
+  g.rtab_bytes = cur;
+  g.rtab_r2s = r2s;
+  g.rtab_mcap = mcap;
+  return RT_OK;
+fail:
+  cudaStreamSynchronize(s);
+  cudaFree(d_r2);
+  cudaFree(d_m);
+  free_row_tables(g);
+  return st;
+#undef CK
 }
 
 }  // namespace asora

@@ -53,6 +53,10 @@ size_t faces_smem_bytes(int hcap, int block) { return group_smem_bytes(hcap, blo
 // (b <= a1, e <= a2), whose flat index in the current layer is not above its
 // own, so each such slot is rewritten in the same round (after the reads) or in
 // a later round -- never before it is read.
+//
+// Row tables: for an item whose window does not clip any layer, the tables of
+// layer m+1 are copied (cp.async) from the precomputed blobs of its R^2 limit
+// while layer m is traced; otherwise warp 0 builds them during layer m.
 template <int GS, bool COLDENS>
 __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int item, const int gt,
                                                 unsigned char* __restrict__ sm, const int h,
@@ -60,8 +64,8 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
   const int cap = (h + 1) * (h + 1);
   double* buf0 = reinterpret_cast<double*>(sm);
   double* buf1 = GS == 32 ? buf0 : buf0 + cap;
-  int* rowpre2 = reinterpret_cast<int*>(buf0 + (GS == 32 ? 1 : 2) * cap);  // [2][h+2]
-  unsigned char* rowof2 = reinterpret_cast<unsigned char*>(rowpre2 + 2 * (h + 2));  // [2][cap]
+  const int TS = row_slot_bytes(h);
+  unsigned char* tab2 = sm + layer_bytes(h, GS == 32);  // [2][TS], 16-byte aligned
   const int wid = gt >> 5, lane = gt & 31;
 
   const int s = item >> 5, f = (item >> 2) & 7, quad = item & 3;
@@ -112,10 +116,27 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
   double* cur = buf1;
   int Hp = 0;
   const bool exit_ok = !COLDENS && a.early_exit;
-  // row tables of layer 1; layer m+1's are built by warp 0 during layer m
-  if (Lmax >= 1 && wid == 0) {
+  // precomputed row tables of this item's R^2 limit, if its window clips no layer:
+  // blob of layer m at a.rtab + toff[m], toff[m+1] - toff[m] bytes
+  const int* toff = nullptr;
+  if (R2 <= a.rtab_max_r2) {
+    const int sl = a.rtab_slot[R2];
+    if (sl >= 0 && a.rtab_hcap[sl] <= min(lim1, lim2)) toff = a.rtab_off + a.rtab_first[sl] - 1;
+  }
+  // row tables of layer 1 (slot 1); layer m+1's (slot (m+1)&1) during layer m
+  if (Lmax >= 1) {
     const int H1 = min(1, isqrt_i(R2 - 1));
-    if (H1 <= h) quad_rows_warp(R2 - 1, H1, min(H1, lim1) + 1, lim2, rowpre2 + (h + 2), rowof2 + cap, lane);
+    if (H1 <= h) {
+      if (toff) {
+        stage_rows<GS>(a.rtab + toff[1], toff[2] - toff[1], tab2 + TS, gt);
+        cp_async_wait_all();
+      } else if (wid == 0) {
+        const int nr = min(H1, lim1) + 1;
+        int* pre = reinterpret_cast<int*>(tab2 + TS);
+        quad_rows_warp(R2 - 1, H1, nr, lim2, pre, reinterpret_cast<unsigned char*>(pre + nr + 1),
+                       lane);
+      }
+    }
   }
   group_sync<GS>();
   for (int m = 1; m <= Lmax; ++m) {
@@ -126,9 +147,15 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
       break;
     }
     const int nrows = min(H, lim1) + 1;
-    const int* rowpre = rowpre2 + (m & 1) * (h + 2);
-    const unsigned char* rowof = rowof2 + (m & 1) * cap;
+    const int* rowpre = reinterpret_cast<const int*>(tab2 + (m & 1) * TS);
+    const unsigned char* rowof = reinterpret_cast<const unsigned char*>(rowpre + nrows + 1);
     const int total = rowpre[nrows];
+    int Hn = 0;  // half-width of the next layer
+    if (m < Lmax) {
+      Hn = min(m + 1, isqrt_i(R2 - (m + 1) * (m + 1)));
+      if (toff && Hn <= h)
+        stage_rows<GS>(a.rtab + toff[m + 1], toff[m + 2] - toff[m + 1], tab2 + ((m + 1) & 1) * TS, gt);
+    }
     const int W = GS == 32 ? h + 1 : H + 1, Wp = GS == 32 ? h + 1 : Hp + 1;
     const int lc = wrapc(cd + sg * m, N);
     const int lay = lc * md;
@@ -188,12 +215,15 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
         }
       }
     }
-    if (wid == 0 && m < Lmax) {  // row tables of the next layer
-      const int rn = R2 - (m + 1) * (m + 1);
-      const int Hn = min(m + 1, isqrt_i(rn));
-      if (Hn <= h)
-        quad_rows_warp(rn, Hn, min(Hn, lim1) + 1, lim2, rowpre2 + ((m + 1) & 1) * (h + 2),
-                       rowof2 + ((m + 1) & 1) * cap, lane);
+    if (m < Lmax && Hn <= h) {  // row tables of the next layer
+      if (toff) {
+        cp_async_wait_all();
+      } else if (wid == 0) {
+        const int nr = min(Hn, lim1) + 1;
+        int* pre = reinterpret_cast<int*>(tab2 + ((m + 1) & 1) * TS);
+        quad_rows_warp(R2 - (m + 1) * (m + 1), Hn, nr, lim2, pre,
+                       reinterpret_cast<unsigned char*>(pre + nr + 1), lane);
+      }
     }
     if (exit_ok) {
       // Exact early exit: if every cell of this layer has tau_out >= 2^E1 (1 + 2^-40),

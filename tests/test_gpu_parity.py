@@ -153,6 +153,17 @@ def test_every_batched_configuration(sched):
         run_both(w, table("bb"), schedules=("batched",), sched=sched)
 
 
+def test_precomputed_row_tables_are_built_for_unclipped_radii():
+    """Sources whose window clips no layer get the precomputed row tables (the
+    results above are identical either way)."""
+    w = S.single_source_uniform()
+    g = make_gpu(w["n"], w["cell_cm"], w["nH"], w["xHI"], w["pos"], w["ndot"], w["radius"],
+                 table("bb"))
+    g.raytrace()
+    assert g.stats()["row_table_bytes"] > 0
+    g.close()
+
+
 def test_degenerate_sizes():
     # one-cell box, radius below one cell, zero rate, huge radius clipped by the window
     for n, R, nd in [(1, 5.0, 1e50), (8, 0.5, 1e50), (8, 100.0, 0.0), (2, 3.0, 1e49)]:
