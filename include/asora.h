@@ -111,6 +111,17 @@ rt_status rt_set_tables(rt_grid_t g, int kind, int E0, int E1, int bits, const d
 rt_status rt_set_density(rt_grid_t g, const double* d_nH);
 rt_status rt_set_xHI(rt_grid_t g, const double* d_xHI);
 
+/* Expanding background (Sec. 4.1.2, Test 2: comoving grid, density diluted by
+ * the expansion).  From this call on, the cell sizes given at creation and the
+ * densities given to rt_set_density are comoving values at scale factor 1: the
+ * ray trace and the chemistry use the proper cell size cell * a and the proper
+ * density n_H * a^-3, with a^-3 evaluated as 1 / (a * a * a) and the products
+ * rounded once each.  Rates are proper (s^-1), column densities proper (cm^-2).
+ * a = 1 (the default) reproduces the static results bit for bit.  a must be
+ * finite and in [1e-6, 1e6] (RT_ERR_INVALID otherwise).  Applies to every box of
+ * an ensemble; synchronises the grid's stream. */
+rt_status rt_set_scale_factor(rt_grid_t g, double a);
+
 /* Sources: d_pos int32[nsrc][3] cell indices (i,j,k) in [0,n), d_box int32[nsrc]
  * box ids (NULL: all in box 0), d_ndot photon rates (s^-1, >= 0), d_radius
  * ray-tracing radius in cells (> 0; cells with |Delta|^2 > floor(R^2) are not

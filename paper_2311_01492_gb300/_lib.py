@@ -47,6 +47,7 @@ SIGNATURES = {
     "rt_set_tables": (_I, [_P, _I, _I, _I, _I, _P, _P]),
     "rt_set_density": (_I, [_P, _P]),
     "rt_set_xHI": (_I, [_P, _P]),
+    "rt_set_scale_factor": (_I, [_P, _D]),
     "rt_set_sources": (_I, [_P, _I, _P, _P, _P, _P]),
     "rt_raytrace": (_I, [_P, _P, _I]),
     "rt_raytrace_source_coldens": (_I, [_P, _I, _P, _I]),

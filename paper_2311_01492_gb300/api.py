@@ -126,6 +126,10 @@ class Grid:
         L.check(self._lib.rt_set_xHI(self._h, _ptr(xHI)), "rt_set_xHI")
         self._keep["xHI"] = xHI
 
+    def set_scale_factor(self, a):
+        """Expanding background: proper cell = cell * a, proper n_H = n_H * a^-3."""
+        L.check(self._lib.rt_set_scale_factor(self._h, float(a)), "rt_set_scale_factor")
+
     def set_sources(self, pos, ndot, radius, box=None):
         pos = pos.to(dtype=torch.int32).contiguous()
         if not pos.is_cuda or pos.dim() != 2 or pos.shape[1] != 3:

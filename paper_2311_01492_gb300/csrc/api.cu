@@ -55,6 +55,14 @@ static void free_grid(Grid* g) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
   } while (0)
 
+// Cell-size dependent constants of a box record.
+static void set_box_cell(BoxDev& B, double c, double sigma0) {
+  B.cell = c;
+  B.inv_cell3 = 1.0 / (c * c * c);
+  B.thin_fac = sigma0 / (c * c);
+  B.sig_cell = sigma0 * c;
+}
+
 static rt_status ensure_geometry(Grid& g, int mmax) {
   if (mmax <= g.geo_mmax) return RT_OK;
   GeoEntry* geo = nullptr;
@@ -284,11 +292,9 @@ rt_status rt_ensemble_create(rt_grid_t* out, int nbox, const int* h_n, const dou
     B.wlo = -(n / 2);
     B.whi = (n % 2 == 0) ? n / 2 - 1 : n / 2;
     B.off = off;
-    B.cell = c;
-    B.inv_cell3 = 1.0 / (c * c * c);
-    B.thin_fac = prm.sigma0_cm2 / (c * c);
-    B.sig_cell = prm.sigma0_cm2 * c;
+    set_box_cell(B, c, prm.sigma0_cm2);
     g->boxes_h.push_back(B);
+    g->cell_comoving.push_back(c);
     off += (int64_t)n * n * n;
     g->nmax = std::max(g->nmax, n);
   }
@@ -393,6 +399,20 @@ static rt_status set_field(rt_grid_t h, const double* d, bool density) {
     return fail(RT_ERR_INVALID, density ? "rt_set_density: n_H must be finite, >= +0 and <= 1e12"
                                         : "rt_set_xHI: x_HI must lie in [+0, 1]");
   if (density) g.nH = d; else g.xHI = d;
+  return RT_OK;
+}
+
+rt_status rt_set_scale_factor(rt_grid_t h, double a) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_set_scale_factor: null grid");
+  if (!(a > 0.0) || !std::isfinite(a) || a > 1e6 || a < 1e-6)
+    return fail(RT_ERR_INVALID, "rt_set_scale_factor: a must be finite and in [1e-6, 1e6]");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  g.a = a;
+  g.inv_a3 = 1.0 / (a * a * a);
+  for (int b = 0; b < g.nbox; ++b) set_box_cell(g.boxes_h[b], g.cell_comoving[b] * a, g.p.sigma0_cm2);
+  TRY(cudaMemcpyAsync(g.boxes_d, g.boxes_h.data(), g.nbox * sizeof(BoxDev), cudaMemcpyHostToDevice,
+                      g.stream));
+  TRY(cudaStreamSynchronize(g.stream));  // the host records may change again
   return RT_OK;
 }
 

@@ -122,6 +122,11 @@ struct Grid {
   double2* gtab = nullptr;
   double2* htab = nullptr;
 
+  // expanding background: proper cell = comoving cell * a, proper n_H = n_H * inv_a3
+  double a = 1.0;
+  double inv_a3 = 1.0;
+  std::vector<double> cell_comoving;  // per box, as created
+
   // inputs (borrowed)
   const double* nH = nullptr;
   const double* xHI = nullptr;

@@ -5,13 +5,14 @@
 // solution of Eq. chemistry is x(t) = x_eq + (x0 - x_eq) exp(-t/t_i) with
 //   1/t_i = Gamma + n_e (C_H + alpha_H),  x_eq = (Gamma + n_e C_H) t_i,
 // and its time average over dt is x_eq + (x0 - x_eq)(1 - exp(-dt/t_i)) t_i/dt.
-// n_e = n_H <x_HII> is iterated to convergence.  Built with --fmad=false so the
-// expressions round exactly as written.
+// n_e = n_H <x_HII> is iterated to convergence; n_H is the proper density (the
+// given one times inv_a3 = a^-3 in an expanding background, an exact no-op for
+// a = 1).  Built with --fmad=false so the expressions round exactly as written.
 #include "asora_internal.cuh"
 
 namespace asora {
 
-__global__ void k_chemistry(int64_t n, const double* __restrict__ nH,
+__global__ void k_chemistry(int64_t n, const double* __restrict__ nH, double inv_a3,
                             const double* __restrict__ gamma, const double* __restrict__ x0,
                             const double* __restrict__ xavg_in, double dt, double alpha_H,
                             double C_H, double tol, int maxit, double conv_tol,
@@ -23,7 +24,7 @@ __global__ void k_chemistry(int64_t n, const double* __restrict__ nH,
        c += (int64_t)gridDim.x * blockDim.x) {
     const double G = gamma[c];
     const double xs = x0[c];
-    const double nh = nH[c];
+    const double nh = nH[c] * inv_a3;
     const double xin = xavg_in[c];
     double xa = xin, xnew = xs;
     for (int it = 0; it < maxit; ++it) {
@@ -62,7 +63,7 @@ cudaError_t launch_chemistry(Grid& g, const double* gamma, const double* x0, con
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t want = (g.ncell + 255) / 256;
   const int grid = (int)std::min<int64_t>(want, (int64_t)sms * 8);
-  k_chemistry<<<grid, 256, 0, g.stream>>>(g.ncell, g.nH, gamma, x0, xavg_in, dt, alpha_H, C_H, tol,
+  k_chemistry<<<grid, 256, 0, g.stream>>>(g.ncell, g.nH, g.inv_a3, gamma, x0, xavg_in, dt, alpha_H, C_H, tol,
                                           maxit, conv_tol, xavg_out, xnew_out,
                                           reinterpret_cast<unsigned long long*>(unconv), skip_flag);
   count_launch();

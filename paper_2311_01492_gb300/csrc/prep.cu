@@ -41,10 +41,13 @@ cudaError_t launch_validate_fields(Grid& g, const double* nH, const double* xHI)
 // One 32x32 tile of the (n^2 rows (i,j)) x (n cols k) matrix of a box:
 // dtau = ((sigma0*cell)*n_H)*x_HI, invn = 1/(n_H*x_HI), and the transposed
 // copy dtauT[k][i][j] so that the z faces read rows of constant k contiguously.
+// n_H is the proper density: the given (comoving) one times inv_a3 = a^-3 in an
+// expanding background (inv_a3 = 1 otherwise, an exact no-op); cell (in the
+// box records) is the proper cell size.
 __global__ void k_precompute(const BoxDev* __restrict__ boxes, const double* __restrict__ nH,
-                             const double* __restrict__ xHI, double* __restrict__ dtau,
-                             double* __restrict__ dtauT, double* __restrict__ invn,
-                             const int* __restrict__ skip) {
+                             const double* __restrict__ xHI, double inv_a3,
+                             double* __restrict__ dtau, double* __restrict__ dtauT,
+                             double* __restrict__ invn, const int* __restrict__ skip) {
   __shared__ double tile[32][33];
   if (skip && *skip) return;
   const BoxDev B = boxes[blockIdx.z];
@@ -59,7 +62,7 @@ __global__ void k_precompute(const BoxDev* __restrict__ boxes, const double* __r
       const int c = c0 + tx;
       if (r < rows && c < n) {
         const int64_t idx = B.off + r * n + c;
-        const double nh = nH[idx], x = xHI[idx];
+        const double nh = nH[idx] * inv_a3, x = xHI[idx];
         const double d = (B.sig_cell * nh) * x;
         dtau[idx] = d;
         invn[idx] = 1.0 / (nh * x);
@@ -79,8 +82,8 @@ __global__ void k_precompute(const BoxDev* __restrict__ boxes, const double* __r
 cudaError_t launch_precompute(Grid& g, const int* skip) {
   const int n = g.nmax;
   dim3 grid((n + 31) / 32, (unsigned)std::min<int64_t>(((int64_t)n * n + 31) / 32, 65535), g.nbox);
-  k_precompute<<<grid, dim3(32, 8), 0, g.stream>>>(g.boxes_d, g.nH, g.xHI, g.dtau, g.dtauT,
-                                                    g.invn, skip);
+  k_precompute<<<grid, dim3(32, 8), 0, g.stream>>>(g.boxes_d, g.nH, g.xHI, g.inv_a3, g.dtau,
+                                                    g.dtauT, g.invn, skip);
   count_launch();
   return cudaGetLastError();
 }

@@ -115,3 +115,66 @@ def test_shadow_behind_a_dense_clump():
     free = assert_rate[c - k, c - k, c]
     assert clump.reshape(n, n, n)[int(round(ci)), int(round(cj)), c]
     assert shadow < 1e-2 * free
+
+
+def test_expanding_background_front():
+    """Test 2 (Sec. 4.1.2): the Test 1 source switched on at z = 9 in a comoving box whose
+    density dilutes as a^-3 (a ∝ t^(2/3)), 10 steps of 50 Myr, proper cell size and density
+    at each step's midpoint (rt_set_scale_factor).  GPU (rt_iterate, CUDA graph) against
+    the oracle's loop with the same fixed iterations (10 per step: the front moves several
+    cells per coarse step), and the comoving I-front radius against the closed form
+    r_S,i y(t)^(1/3)."""
+    T2_ITERS = 10
+    import json
+    import os
+    from oracle import cosmology as Cm
+    from paper_2311_01492_gb300 import api
+    with open(os.path.join(os.path.dirname(__file__), "golden", "cosmo_stromgren_test2.json")) as f:
+        gd = json.load(f)
+    inp, rd = gd["inputs"], gd["readings"]
+    n = 48
+    t_i = Cm.age_eds(inp["z_i"], inp["h"], inp["Omega_M"])
+    dt = 50.0 * S.MYR_S
+    cell_c = rd["box_cm"] / n
+    c = n // 2
+    nH_c = np.full(n ** 3, inp["n_H_i_cm3"])
+    pos, ndot, R = np.array([[c, c, c]], np.int32), np.array([inp["Ndot_s"]]), np.array([n / 2 - 0.5])
+    tab = O.make_table("grey_exact")
+    g = api.Grid(n, cell_c)
+    g.set_tables("grey_exact")
+    g.set_density(dev(nH_c))
+    g.set_sources(dev(pos, torch.int32), dev(ndot), dev(R))
+    xg = dev(np.zeros(n ** 3))
+    xo = np.zeros(n ** 3)
+    t_rec = 1.0 / (inp["alpha_H_cm3_s"] * inp["n_H_i_cm3"])
+    r_S = Cm.stromgren_radius(inp["Ndot_s"], inp["n_H_i_cm3"], inp["alpha_H_cm3_s"])
+    t = t_i
+    for step in range(10):
+        a = Cm.scale_factor(t + 0.5 * dt, t_i)
+        g.set_scale_factor(a)
+        _, it = g.iterate(xg, dt, max_iter=T2_ITERS, conv_frac=0.0, use_graph=True)
+        assert it == T2_ITERS
+        nH = nH_c * (1.0 / (a * a * a))
+        cell = cell_c * a
+        xa = xo.copy()
+        for _ in range(T2_ITERS):
+            G = O.raytrace(n, cell, nH, 1.0 - xa, pos, ndot, R, tab, nthreads=8)["gamma"]
+            xa, xn, _ = O.chemistry(nH, xo, xa, G, dt, alpha_H=inp["alpha_H_cm3_s"])
+        xo = xn
+        t += dt
+        x3 = xg.cpu().numpy()
+        np.testing.assert_allclose(x3, xo, rtol=1e-6, atol=1e-12)
+        xhi = 1.0 - x3.reshape(n, n, n)[c:, c, c]
+        k = int(np.argmax(xhi > 0.5))
+        r = (k - 1 + (0.5 - xhi[k - 1]) / (xhi[k] - xhi[k - 1])) * cell_c
+        ana = r_S * Cm.y_closed_form(t, t_i, t_rec) ** (1 / 3)
+        assert abs(r / ana - 1) < (0.01 if step >= 2 else 0.02), (step, r / ana)
+    # a = 1 restores the static grid bit for bit
+    g.set_scale_factor(1.0)
+    g.set_xHI(dev(np.full(n ** 3, 0.5)))
+    ref = O.raytrace(n, cell_c, nH_c, np.full(n ** 3, 0.5), pos, ndot, R, tab)
+    assert np.array_equal(g.source_coldens(0).cpu().numpy(),
+                          O.raytrace(n, cell_c, nH_c, np.full(n ** 3, 0.5), pos, ndot, R, tab,
+                                     gamma=False, coldens_src=0)["coldens"])
+    np.testing.assert_allclose(g.raytrace().cpu().numpy(), ref["gamma"], rtol=1e-9, atol=0)
+    g.close()

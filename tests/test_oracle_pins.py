@@ -481,3 +481,105 @@ def test_complex_step_matches_finite_differences():
         Ls = O.raytrace(n, cell, nH, xHI, pos[s:s + 1], ndot[s:s + 1], R[s:s + 1], tab,
                         gamma=False, wloss=w)["loss"]
         assert dq[s] == pytest.approx(Ls, rel=1e-12)
+
+
+# ------------------------------------- Stromgren in an expanding background (Sec. 4.1.2)
+def _golden2():
+    with open(os.path.join(HERE, "golden", "cosmo_stromgren_test2.json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("lam", [0.05, 0.866, 3.0, 20.0])
+def test_cosmological_y_closed_form_matches_its_ode(lam):
+    """The E2 closed form of (r_I/r_S,i)^3 equals the numerical solution of the photon
+    balance dy/dt = (1 - y (t_i/t)^2)/t_rec,i, y(t_i) = 0."""
+    from oracle import cosmology as Cm
+    t_i = 1.0
+    t_rec = t_i / lam
+    for f in [1.001, 1.1, 1.5, 2.0, 4.0, 10.0]:
+        a, b = Cm.y_closed_form(f * t_i, t_i, t_rec), Cm.y_ode(f * t_i, t_i, t_rec)
+        assert a == pytest.approx(b, rel=1e-9), (lam, f)
+
+
+def test_cosmological_y_limits():
+    from oracle import cosmology as Cm
+    # just after ignition nothing has recombined: y = (t - t_i)/t_rec,i
+    assert Cm.y_closed_form(1.0 + 1e-6, 1.0, 2.0) == pytest.approx(0.5e-6, rel=1e-5)
+    # fast recombination: y relaxes onto the equilibrium a^3 = (t/t_i)^2 with lag
+    # (d/dt a^3) t_rec (t/t_i)^2, i.e. y(2 t_i) = 4 - 16 t_rec/t_i + O(t_rec^2)
+    lam = 300.0
+    y = Cm.y_closed_form(2.0, 1.0, 1.0 / lam)
+    assert (4.0 - y) * lam == pytest.approx(16.0, rel=0.03)
+    # expansion makes the front larger than in a static medium of the initial density
+    t_i, t_rec = 1.0, 1.0
+    for f in [1.5, 2.0, 3.0]:
+        assert Cm.y_closed_form(f, t_i, t_rec) > 1.0 - math.exp(-(f - t_i) / t_rec)
+
+
+def test_cosmological_constants():
+    """Test 2's numbers: ignition at z = 9 of the printed cosmology (age ~ 567 Myr in the
+    matter-dominated expansion), t_rec,i and r_S,i of the Test 1 source."""
+    from oracle import cosmology as Cm
+    inp = _golden2()["inputs"]
+    t_i = Cm.age_eds(inp["z_i"], inp["h"], inp["Omega_M"])
+    assert 560 < t_i / S.MYR_S < 575
+    t_rec = 1.0 / (inp["alpha_H_cm3_s"] * inp["n_H_i_cm3"])
+    assert 650 < t_rec / S.MYR_S < 660
+    r_S = Cm.stromgren_radius(inp["Ndot_s"], inp["n_H_i_cm3"], inp["alpha_H_cm3_s"])
+    assert 0.4 < r_S / _golden2()["readings"]["box_cm"] < 0.45
+
+
+def cosmo_stromgren_run(n=32, dt_myr=50.0, max_iter=30, expand=True):
+    """Test 2 (Sec. 4.1.2) with the oracle: comoving grid, proper cell size and density at
+    the midpoint of every step, RT <-> chemistry; comoving I-front radius after each step."""
+    from oracle import cosmology as Cm
+    gd = _golden2()
+    inp, rd = gd["inputs"], gd["readings"]
+    t_i = Cm.age_eds(inp["z_i"], inp["h"], inp["Omega_M"])
+    cell_c = rd["box_cm"] / n
+    c = n // 2
+    nH_c = np.full(n ** 3, inp["n_H_i_cm3"])
+    x = np.zeros(n ** 3)
+    tab = O.make_table("grey_exact")
+    dt = dt_myr * S.MYR_S
+    out = []
+    t = t_i
+    while t < t_i + inp["t_evo_Myr"] * S.MYR_S - 1e-6 * dt:
+        a = Cm.scale_factor(t + 0.5 * dt, t_i) if expand else 1.0
+        nH = nH_c * (1.0 / (a * a * a))
+        cell = cell_c * a
+        xa = x.copy()
+        for it in range(max_iter):
+            G = O.raytrace(n, cell, nH, 1.0 - xa, [[c, c, c]], [inp["Ndot_s"]], [n / 2.0 - 0.5],
+                           tab)["gamma"]
+            xa, xn, unconv = O.chemistry(nH, x, xa, G, dt, alpha_H=inp["alpha_H_cm3_s"])
+            if unconv < 1e-4 * n ** 3 and it > 0:
+                break
+        x = xn
+        t += dt
+        xhi = 1.0 - x.reshape(n, n, n)[c:, c, c]
+        k = int(np.argmax(xhi > 0.5))
+        r = (k - 1 + (0.5 - xhi[k - 1]) / (xhi[k] - xhi[k - 1])) * cell_c if k > 0 else 0.0
+        out.append((t, r))
+    return t_i, out
+
+
+def test_cosmological_ifront_radius():
+    """Comoving I-front radius vs r_S,i y(t)^(1/3) (Sec. 4.1.2): within 3 % after the first
+    coarse step and 1 % from 250 Myr on, while the static solution (Eq. rI1) misses the
+    final radius by more than 5 % -- and a run without expansion misses the closed form."""
+    from oracle import cosmology as Cm
+    inp = _golden2()["inputs"]
+    t_rec = 1.0 / (inp["alpha_H_cm3_s"] * inp["n_H_i_cm3"])
+    r_S = Cm.stromgren_radius(inp["Ndot_s"], inp["n_H_i_cm3"], inp["alpha_H_cm3_s"])
+    t_i, out = cosmo_stromgren_run()
+    for t, r in out:
+        ana = r_S * Cm.y_closed_form(t, t_i, t_rec) ** (1 / 3)
+        assert abs(r / ana - 1) < (0.01 if t - t_i >= 250 * S.MYR_S - 1 else 0.03), (
+            (t - t_i) / S.MYR_S, r / ana)
+    t, r = out[-1]
+    static = r_S * (1 - math.exp(-(t - t_i) / t_rec)) ** (1 / 3)
+    assert r / static > 1.05
+    _, out_static = cosmo_stromgren_run(expand=False)
+    t, r = out_static[-1]
+    assert r / (r_S * Cm.y_closed_form(t, t_i, t_rec) ** (1 / 3)) < 0.96
