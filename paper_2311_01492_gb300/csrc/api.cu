@@ -38,11 +38,11 @@ static int isqrt_h(int64_t x) {
 static void free_grid(Grid* g) {
   cudaFree(g->boxes_d); cudaFree(g->gtab); cudaFree(g->htab);
   cudaFree(g->dtau); cudaFree(g->dtauT); cudaFree(g->invn);
-  cudaFree(g->src); cudaFree(g->ndot); cudaFree(g->r2lim); cudaFree(g->items);
-  cudaFree(g->src_of_input); cudaFree(g->geo); cudaFree(g->georow); cudaFree(g->queue); cudaFree(g->err);
+  free_sources(*g);
+  cudaFree(g->geo); cudaFree(g->georow); cudaFree(g->queue); cudaFree(g->err);
   cudaFree(g->cube); cudaFree(g->unconv); cudaFree(g->xbuf); cudaFree(g->xavg);
   cudaFree(g->xavg2); cudaFree(g->xhi_int); cudaFree(g->flags); cudaFree(g->counters);
-  cudaFree(g->ndot_in); cudaFree(g->bwd_stack); cudaFree(g->dq_merged);
+  cudaFree(g->bwd_stack); cudaFree(g->dq_merged);
   free_row_tables(*g);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);

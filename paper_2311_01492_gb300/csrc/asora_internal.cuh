@@ -149,6 +149,24 @@ struct Grid {
   int max_r2 = 0;
   int64_t source_voxels = 0;
   std::vector<int> r2_sorted_h;  // per merged source (LPT order), host copy
+  size_t src_cap = 0;            // sources the arrays above (and items / 24) can hold
+  // scratch of the source ingest, kept between calls and grown on demand
+  struct Ingest {
+    size_t cap = 0;  // sources the per-source arrays hold
+    uint64_t *keys = nullptr, *keys2 = nullptr;
+    int *idx = nullptr, *idx2 = nullptr, *r2in = nullptr, *head = nullptr, *mid = nullptr;
+    SrcDev* msrc = nullptr;
+    double* mndot = nullptr;
+    int* mr2 = nullptr;
+    uint32_t *lkey = nullptr, *lkey2 = nullptr;
+    int *lval = nullptr, *order = nullptr, *lpt = nullptr;
+    void* tmp = nullptr;
+    size_t tmp_bytes = 0;
+    int* dscal = nullptr;      // device scalars: [0] largest r2
+    int* hscal = nullptr;      // pinned host: error bits, last head, last offset, largest r2
+    int* r2pin = nullptr;      // pinned host: r2 per merged source
+    SrcDev* srcpin = nullptr;  // pinned host: merged sources (ensembles)
+  } ing;
 
   // precomputed row tables of the batched trace (see TraceArgs::rtab)
   unsigned char* rtab = nullptr;
@@ -195,6 +213,9 @@ struct Grid {
 
 // Kernels launched by this library in this process (host-side count).
 void count_launch(int n = 1);
+
+// Frees the source arrays and the ingest scratch (prep.cu).
+void free_sources(Grid& g);
 
 // Row tables for the distinct R^2 limits of the ingested sources (prep.cu);
 // kept while the set of limits and the window size do not change.

@@ -271,115 +271,138 @@ static int64_t ball_count(int r2, int n) {
     }                                           \
   } while (0)
 
+void free_sources(Grid& g) {
+  Grid::Ingest& w = g.ing;
+  cudaFree(g.src); cudaFree(g.ndot); cudaFree(g.r2lim); cudaFree(g.items);
+  cudaFree(g.src_of_input); cudaFree(g.ndot_in);
+  g.src = nullptr; g.ndot = nullptr; g.r2lim = nullptr; g.items = nullptr;
+  g.src_of_input = nullptr; g.ndot_in = nullptr;
+  g.src_cap = 0;
+  cudaFree(w.keys); cudaFree(w.keys2); cudaFree(w.idx); cudaFree(w.idx2); cudaFree(w.r2in);
+  cudaFree(w.head); cudaFree(w.mid); cudaFree(w.msrc); cudaFree(w.mndot); cudaFree(w.mr2);
+  cudaFree(w.lkey); cudaFree(w.lkey2); cudaFree(w.lval); cudaFree(w.order); cudaFree(w.lpt);
+  cudaFree(w.tmp); cudaFree(w.dscal);
+  cudaFreeHost(w.hscal); cudaFreeHost(w.r2pin); cudaFreeHost(w.srcpin);
+  w = Grid::Ingest{};
+}
+
+// Grow the per-source arrays (ingest scratch and the ingested sources) to n sources.
+static cudaError_t reserve_sources(Grid& g, size_t n) {
+  Grid::Ingest& w = g.ing;
+  if (n <= w.cap && n <= g.src_cap) return cudaSuccess;
+  cudaStreamSynchronize(g.stream);  // earlier work may still read the old arrays
+  free_sources(g);
+  cudaError_t e = cudaSuccess;
+  auto dm = [&](auto*& p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p), bytes);
+  };
+  dm(w.keys, n * sizeof(uint64_t)); dm(w.keys2, n * sizeof(uint64_t));
+  dm(w.idx, n * sizeof(int)); dm(w.idx2, n * sizeof(int)); dm(w.r2in, n * sizeof(int));
+  dm(w.head, n * sizeof(int)); dm(w.mid, n * sizeof(int));
+  dm(w.msrc, n * sizeof(SrcDev)); dm(w.mndot, n * sizeof(double)); dm(w.mr2, n * sizeof(int));
+  dm(w.lkey, n * sizeof(uint32_t)); dm(w.lkey2, n * sizeof(uint32_t));
+  dm(w.lval, n * sizeof(int)); dm(w.order, n * sizeof(int)); dm(w.lpt, n * sizeof(int));
+  dm(w.dscal, 4 * sizeof(int));
+  dm(g.src, n * sizeof(SrcDev)); dm(g.ndot, n * sizeof(double)); dm(g.r2lim, n * sizeof(int));
+  dm(g.items, 24 * n * sizeof(int)); dm(g.src_of_input, n * sizeof(int));
+  dm(g.ndot_in, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&w.hscal), 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&w.r2pin), n * sizeof(int));
+  if (e == cudaSuccess && g.nbox > 1)
+    e = cudaMallocHost(reinterpret_cast<void**>(&w.srcpin), n * sizeof(SrcDev));
+  // CUB scratch for the largest of its three uses at n items
+  size_t need = 0, tb = 0;
+  if (e == cudaSuccess) e = cub::DeviceRadixSort::SortPairs(nullptr, need, w.keys, w.keys2, w.idx,
+                                                            w.idx2, (int)n, 0, 64, g.stream);
+  tb = std::max(tb, need);
+  if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(nullptr, need, w.head, w.mid, (int)n,
+                                                          g.stream);
+  tb = std::max(tb, need);
+  if (e == cudaSuccess) e = cub::DeviceRadixSort::SortPairs(nullptr, need, w.lkey, w.lkey2, w.lval,
+                                                            w.order, (int)n, 0, 32, g.stream);
+  tb = std::max(tb, need);
+  if (e == cudaSuccess) e = cub::DeviceReduce::Max(nullptr, need, w.r2in, w.dscal, (int)n,
+                                                   g.stream);
+  tb = std::max(tb, need);
+  dm(w.tmp, tb);
+  if (e != cudaSuccess) {
+    free_sources(g);
+    return e;
+  }
+  w.tmp_bytes = tb;
+  w.cap = n;
+  g.src_cap = n;
+  return cudaSuccess;
+}
+
 rt_status ingest_sources(Grid& g, int nsrc, const int32_t* d_pos, const int32_t* d_box,
                          const double* d_ndot, const double* d_radius) {
   rt_status st = RT_OK;
   cudaStream_t s = g.stream;
-  uint64_t *keys = nullptr, *keys2 = nullptr;
-  int *idx = nullptr, *idx2 = nullptr, *r2in = nullptr, *head = nullptr, *mid = nullptr;
-  SrcDev* msrc = nullptr;
-  double* mndot = nullptr;
-  int* mr2 = nullptr;
-  uint32_t *lkey = nullptr, *lkey2 = nullptr;
-  int *lval = nullptr, *order = nullptr, *lpt_of_merged = nullptr;
-  void* tmp = nullptr;
-  size_t tmp_bytes = 0, need = 0;
-  int nm = 0, last_head = 0, last_mid = 0;
-  int herr = 0;
+  Grid::Ingest& w = g.ing;
+  size_t need = 0;
+  int nm = 0;
   const int T = 256;
   const int nb = (nsrc + T - 1) / T;
 
-  // free previous sources
-  cudaFree(g.src); cudaFree(g.ndot); cudaFree(g.r2lim); cudaFree(g.items); cudaFree(g.src_of_input);
-  cudaFree(g.ndot_in);
-  g.src = nullptr; g.ndot = nullptr; g.r2lim = nullptr; g.items = nullptr; g.src_of_input = nullptr;
-  g.ndot_in = nullptr;
   g.nsrc = 0; g.nsrc_in = 0; g.max_r2 = 0; g.source_voxels = 0; g.r2_sorted_h.clear();
   if (nsrc == 0) return RT_OK;
+  CK(reserve_sources(g, (size_t)nsrc));
 
-  CK(cudaMalloc(&keys, nsrc * sizeof(uint64_t)));
-  CK(cudaMalloc(&keys2, nsrc * sizeof(uint64_t)));
-  CK(cudaMalloc(&idx, nsrc * sizeof(int)));
-  CK(cudaMalloc(&idx2, nsrc * sizeof(int)));
-  CK(cudaMalloc(&r2in, nsrc * sizeof(int)));
-  CK(cudaMalloc(&head, nsrc * sizeof(int)));
-  CK(cudaMalloc(&mid, nsrc * sizeof(int)));
   CK(cudaMemsetAsync(g.err, 0, sizeof(int), s));
-  k_src_keys<<<nb, T, 0, s>>>(g.boxes_d, g.nbox, nsrc, d_pos, d_box, d_ndot, d_radius, keys, idx,
-                              r2in, g.err);
+  k_src_keys<<<nb, T, 0, s>>>(g.boxes_d, g.nbox, nsrc, d_pos, d_box, d_ndot, d_radius, w.keys,
+                              w.idx, w.r2in, g.err);
   count_launch();
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(&herr, g.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  // stable sort by (cell, r2): co-located sources with equal radius become adjacent
+  // (keys of invalid sources are harmless: they are reported below before any use)
+  need = w.tmp_bytes;
+  CK(cub::DeviceRadixSort::SortPairs(w.tmp, need, w.keys, w.keys2, w.idx, w.idx2, nsrc, 0, 64, s));
+  k_src_heads<<<nb, T, 0, s>>>(w.keys2, nsrc, w.head);
+  count_launch();
+  CK(cudaGetLastError());
+  need = w.tmp_bytes;
+  CK(cub::DeviceScan::ExclusiveSum(w.tmp, need, w.head, w.mid, nsrc, s));
+  need = w.tmp_bytes;
+  CK(cub::DeviceReduce::Max(w.tmp, need, w.r2in, w.dscal, nsrc, s));  // for the LPT key
+  CK(cudaMemcpyAsync(w.hscal + 0, g.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(w.hscal + 1, w.head + nsrc - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(w.hscal + 2, w.mid + nsrc - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(w.hscal + 3, w.dscal, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (herr) {
+  if (w.hscal[0]) {
     st = fail(RT_ERR_INVALID, "rt_set_sources: source outside its box, bad box id, radius <= 0 "
                               "or non-finite/negative photon rate");
     goto done;
   }
-  // stable sort by (cell, r2): co-located sources with equal radius become adjacent
-  CK(cub::DeviceRadixSort::SortPairs(nullptr, need, keys, keys2, idx, idx2, nsrc, 0, 64, s));
-  tmp_bytes = need;
-  CK(cub::DeviceScan::ExclusiveSum(nullptr, need, head, mid, nsrc, s));
-  tmp_bytes = std::max(tmp_bytes, need);
-  CK(cub::DeviceRadixSort::SortPairs(nullptr, need, lkey, lkey2, lval, order, nsrc, 0, 32, s));
-  tmp_bytes = std::max(tmp_bytes, need);
-  CK(cudaMalloc(&tmp, tmp_bytes));
-  need = tmp_bytes;
-  CK(cub::DeviceRadixSort::SortPairs(tmp, need, keys, keys2, idx, idx2, nsrc, 0, 64, s));
-  k_src_heads<<<nb, T, 0, s>>>(keys2, nsrc, head);
-  count_launch();
-  CK(cudaGetLastError());
-  need = tmp_bytes;
-  CK(cub::DeviceScan::ExclusiveSum(tmp, need, head, mid, nsrc, s));
-  CK(cudaMemcpyAsync(&last_head, head + nsrc - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&last_mid, mid + nsrc - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  nm = last_mid + last_head;
-  {
-    // max r2 for the LPT key
-    std::vector<int> r2h(nsrc);
-    CK(cudaMemcpy(r2h.data(), r2in, nsrc * sizeof(int), cudaMemcpyDeviceToHost));
-    for (int v : r2h) g.max_r2 = std::max(g.max_r2, v);
-  }
-  CK(cudaMalloc(&msrc, nm * sizeof(SrcDev)));
-  CK(cudaMalloc(&mndot, nm * sizeof(double)));
-  CK(cudaMalloc(&mr2, nm * sizeof(int)));
-  CK(cudaMalloc(&lkey, nm * sizeof(uint32_t)));
-  CK(cudaMalloc(&lkey2, nm * sizeof(uint32_t)));
-  CK(cudaMalloc(&lval, nm * sizeof(int)));
-  CK(cudaMalloc(&order, nm * sizeof(int)));
-  CK(cudaMalloc(&lpt_of_merged, nm * sizeof(int)));
-  CK(cudaMalloc(&g.src_of_input, nsrc * sizeof(int)));
-  CK(cudaMalloc(&g.ndot_in, nsrc * sizeof(double)));
+  nm = w.hscal[2] + w.hscal[1];
+  g.max_r2 = w.hscal[3];
   CK(cudaMemcpyAsync(g.ndot_in, d_ndot, nsrc * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  k_src_merge<<<nb, T, 0, s>>>(keys2, idx2, head, mid, nsrc, d_pos, d_box, d_ndot, r2in, msrc,
-                               mndot, mr2, lkey, lval, g.src_of_input, g.max_r2);
+  k_src_merge<<<nb, T, 0, s>>>(w.keys2, w.idx2, w.head, w.mid, nsrc, d_pos, d_box, d_ndot, w.r2in,
+                               w.msrc, w.mndot, w.mr2, w.lkey, w.lval, g.src_of_input, g.max_r2);
   count_launch();
   CK(cudaGetLastError());
-  need = tmp_bytes;
-  CK(cub::DeviceRadixSort::SortPairs(tmp, need, lkey, lkey2, lval, order, nm, 0, 32, s));
-  CK(cudaMalloc(&g.src, nm * sizeof(SrcDev)));
-  CK(cudaMalloc(&g.ndot, nm * sizeof(double)));
-  CK(cudaMalloc(&g.r2lim, nm * sizeof(int)));
-  CK(cudaMalloc(&g.items, (size_t)24 * nm * sizeof(int)));
-  k_src_order<<<(nm + T - 1) / T, T, 0, s>>>(order, nm, msrc, mndot, mr2, g.src, g.ndot, g.r2lim,
-                                             g.items, lpt_of_merged);
+  need = w.tmp_bytes;
+  CK(cub::DeviceRadixSort::SortPairs(w.tmp, need, w.lkey, w.lkey2, w.lval, w.order, nm, 0, 32, s));
+  k_src_order<<<(nm + T - 1) / T, T, 0, s>>>(w.order, nm, w.msrc, w.mndot, w.mr2, g.src, g.ndot,
+                                             g.r2lim, g.items, w.lpt);
   count_launch();
   CK(cudaGetLastError());
-  k_remap<<<nb, T, 0, s>>>(g.src_of_input, lpt_of_merged, nsrc);
+  k_remap<<<nb, T, 0, s>>>(g.src_of_input, w.lpt, nsrc);
   count_launch();
   CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(w.r2pin, g.r2lim, nm * sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (g.nbox > 1)
+    CK(cudaMemcpyAsync(w.srcpin, g.src, nm * sizeof(SrcDev), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   {
-    g.r2_sorted_h.resize(nm);
-    std::vector<SrcDev> sh(nm);
-    CK(cudaMemcpyAsync(g.r2_sorted_h.data(), g.r2lim, nm * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(sh.data(), g.src, nm * sizeof(SrcDev), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    g.r2_sorted_h.assign(w.r2pin, w.r2pin + nm);
     std::map<std::pair<int, int>, int64_t> memo;
     int64_t sv = 0, last_cnt = 0;
     std::pair<int, int> last_key(-1, -1);
     for (int p = 0; p < nm; ++p) {  // sources come sorted by r2: runs of equal keys
-      const auto key = std::make_pair(g.r2_sorted_h[p], g.boxes_h[sh[p].box].n);
+      const int box = g.nbox > 1 ? w.srcpin[p].box : 0;
+      const auto key = std::make_pair(g.r2_sorted_h[p], g.boxes_h[box].n);
       if (key != last_key) {
         auto it = memo.find(key);
         if (it == memo.end()) it = memo.emplace(key, ball_count(key.first, key.second)).first;
@@ -393,10 +416,6 @@ rt_status ingest_sources(Grid& g, int nsrc, const int32_t* d_pos, const int32_t*
   g.nsrc = nm;
   g.nsrc_in = nsrc;
 done:
-  cudaFree(keys); cudaFree(keys2); cudaFree(idx); cudaFree(idx2); cudaFree(r2in);
-  cudaFree(head); cudaFree(mid); cudaFree(msrc); cudaFree(mndot); cudaFree(mr2);
-  cudaFree(lkey); cudaFree(lkey2); cudaFree(lval); cudaFree(order); cudaFree(lpt_of_merged);
-  cudaFree(tmp);
   return st;
 }
 
