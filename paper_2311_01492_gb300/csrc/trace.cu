@@ -24,10 +24,13 @@
 // (|Delta_d| equal to another |Delta|) gets the same value from every face
 // that contains it, because the weights of its out-of-face interpolants are
 // exactly zero; each face therefore traces its closed pyramid independently
-// and only the owning face (k before j before i) deposits the rate.  The six
-// faces of every source are independent work items taken longest-first from
-// a device queue by persistent CTAs; each layer lives in shared memory (two
-// buffers of (2H+1)^2 doubles), so a cell reads only the previous layer.
+// and only the owning face (k before j before i) deposits the rate.  Each face
+// splits again into four quadrants (see trace_face_item), so every source
+// gives 24 independent work items, taken longest-first from a device queue by
+// persistent groups: CTAs (k_trace_faces) for items with wide layers, single
+// warps (k_trace_faces_warp) for the others.  A quadrant layer lives in shared
+// memory ((H+1)^2 doubles; two buffers per CTA, one updated in place per
+// warp), so a cell reads only the previous layer of its own item.
 #include <algorithm>
 #include <cmath>
 
