@@ -78,6 +78,30 @@ def test_adjoint_matches_oracle_complex_step(spec, xhi_scale, stop):
     g.close()
 
 
+def test_adjoint_in_an_expanding_background():
+    """With a scale factor the gradients are those of the proper-unit problem: the oracle's
+    complex-step derivatives at proper cell size cell*a and density n_H*a^-3 (the
+    derivative w.r.t. log n_HI is the same for comoving and proper densities)."""
+    n = 12
+    cell = 10 * S.KPC_CM
+    a = 1.37
+    nH, xHI, pos, ndot, R, w = _box(n, 43, 3e-3, 4)
+    tab = O.make_table("bb")
+    g = gpu_grid(n, cell, nH, xHI, pos, ndot, R, tab)
+    g.set_scale_factor(a)
+    dn, dq = g.backward(dev(w))
+    dn, dq = dn.cpu().numpy(), dq.cpu().numpy()
+    g.stats()
+    cells = np.arange(n ** 3, dtype=np.int64)
+    dn_o, dq_o = O.loss_grad_cs(n, cell * a, nH * (1.0 / (a * a * a)), xHI, pos, ndot, R, tab, w,
+                                cells, np.arange(len(ndot)), nthreads=8)
+    scale = np.abs(dn_o).max()
+    assert scale > 0
+    np.testing.assert_allclose(dn, dn_o, rtol=1e-9, atol=1e-12 * scale)
+    np.testing.assert_allclose(dq, dq_o, rtol=1e-9, atol=1e-12 * np.abs(dq_o).max())
+    g.close()
+
+
 def _loss(g, w):
     gam = g.raytrace().cpu().numpy()
     return math.fsum(w * gam)
