@@ -224,8 +224,18 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
       g.stats.launches += 1;
     }
     if (split < n_items) {
-      const size_t smem = faces_smem_bytes(hsm, 32) * g.warps_per_block;
-      const int maxg = faces_max_grid(32, smem);
+      // warp mode: CTAs of 8 or 4 warps, whichever keeps more warps resident (a
+      // warp's shared memory grows with its layer capacity; smaller CTAs pack better)
+      int wpb = 8, maxg = 0;
+      for (int cand : {8, 4}) {
+        const int mg = faces_max_grid(32, faces_smem_bytes(hsm, 32) * cand, cand);
+        if (mg * cand > maxg * wpb) {
+          maxg = mg;
+          wpb = cand;
+        }
+      }
+      g.warps_per_block = wpb;
+      const size_t smem = faces_smem_bytes(hsm, 32) * wpb;
       if (maxg <= 0) return fail(RT_ERR_CUDA, "rt_raytrace: no occupancy for the warp face kernel");
       TraceArgs b = a;
       b.hcap = hsm;
@@ -233,8 +243,8 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
       b.n_items = n_items;
       b.queue = g.queue + 1;
       const int nitem = n_items - split;
-      const int grid = std::max(1, std::min((nitem + g.warps_per_block - 1) / g.warps_per_block, maxg));
-      TRY(launch_trace_faces(g, b, 32, grid, smem));
+      const int grid = std::max(1, std::min((nitem + wpb - 1) / wpb, maxg));
+      TRY(launch_trace_faces(g, b, 32, grid, smem, wpb));
       g.stats.launches += 1;
       if (split == 0) {
         g.stats.block = 32;

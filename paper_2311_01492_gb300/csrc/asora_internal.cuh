@@ -197,7 +197,7 @@ struct Grid {
   int* flags = nullptr;
   int block_big = 128;      // threads per CTA for large-source items
   int hsmall = 19;          // items whose layers fit this half-width run one per warp
-  int warps_per_block = 8;  // warp-mode CTA size (fixed by the kernel template)
+  int warps_per_block = 8;  // warp-mode CTA size of the last trace (4 or 8)
   unsigned long long* counters = nullptr;  // [0]: rate evaluations of the last trace
   double2* bwd_stack = nullptr;  // adjoint: per-CTA (tau_in, tau_out) stacks
   size_t bwd_stack_bytes = 0;
@@ -231,10 +231,11 @@ cudaError_t launch_precompute(Grid& g, const int* skip = nullptr);
 cudaError_t launch_zero(double* p, int64_t n, const int* skip, cudaStream_t s);
 cudaError_t launch_validate_fields(Grid& g, const double* nH, const double* xHI);
 cudaError_t launch_geometry(GeoEntry* geo, GeoRow* georow, int mmax, cudaStream_t s);
-cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid, size_t smem);
+cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid, size_t smem,
+                               int wpb = 8);  // wpb: warps per CTA in warp mode (block 32)
 cudaError_t launch_trace_shells(Grid& g, const TraceArgs& a, int block, int grid);
 size_t faces_smem_bytes(int hcap, int block);  // per CTA (block 32: per warp)
-int faces_max_grid(int block, size_t smem);
+int faces_max_grid(int block, size_t smem, int wpb = 8);
 int shells_max_grid(int block);
 rt_status ingest_sources(Grid& g, int nsrc, const int32_t* d_pos, const int32_t* d_box,
                          const double* d_ndot, const double* d_radius);

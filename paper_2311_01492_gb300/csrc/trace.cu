@@ -301,14 +301,16 @@ __global__ void __launch_bounds__(WPB * 32, 1024 / (WPB * 32)) k_trace_faces_war
   flush_rate_count(a, nrate);
 }
 
-constexpr int kWarpsPerBlock = 8;
-
-// Kernel variant for (block, coldens); block 32 = warp mode.  Null if not
-// instantiated.
-static const void* face_kernel(int block, bool coldens) {
+// Kernel variant for (block, warps per CTA, coldens); block 32 = warp mode with
+// wpb warps per CTA (4 or 8).  Null if not instantiated.
+static const void* face_kernel(int block, int wpb, bool coldens) {
   switch (block) {
-    case 32: return coldens ? (const void*)k_trace_faces_warp<kWarpsPerBlock, true>
-                            : (const void*)k_trace_faces_warp<kWarpsPerBlock, false>;
+    case 32:
+      if (wpb == 4) return coldens ? (const void*)k_trace_faces_warp<4, true>
+                                   : (const void*)k_trace_faces_warp<4, false>;
+      if (wpb == 8) return coldens ? (const void*)k_trace_faces_warp<8, true>
+                                   : (const void*)k_trace_faces_warp<8, false>;
+      return nullptr;
     case 128: return coldens ? (const void*)k_trace_faces<128, true>
                              : (const void*)k_trace_faces<128, false>;
     case 256: return coldens ? (const void*)k_trace_faces<256, true>
@@ -317,13 +319,14 @@ static const void* face_kernel(int block, bool coldens) {
   }
 }
 
-cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid, size_t smem) {
+cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid, size_t smem,
+                               int wpb) {
   const bool cd = a.coldens != nullptr;
-  const void* fn = face_kernel(block, cd);
+  const void* fn = face_kernel(block, wpb, cd);
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int threads = block == 32 ? kWarpsPerBlock * 32 : block;
+  const int threads = block == 32 ? wpb * 32 : block;
   TraceArgs arg = a;
   void* params[] = {&arg};
   e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), params, smem, g.stream);
@@ -331,13 +334,13 @@ cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid,
   return e;
 }
 
-int faces_max_grid(int block, size_t smem) {
+int faces_max_grid(int block, size_t smem, int wpb) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const void* fn = face_kernel(block, false);
+  const void* fn = face_kernel(block, wpb, false);
   if (!fn) return 0;
-  const int threads = block == 32 ? kWarpsPerBlock * 32 : block;
+  const int threads = block == 32 ? wpb * 32 : block;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
   if (e != cudaSuccess) return 0;
