@@ -206,7 +206,7 @@ typedef struct {
 rt_status rt_set_schedule(rt_grid_t g, int block_big, int hsmall);
 
 /* Autotuner of RT_SCHED_BATCHED: times rt_raytrace on the registered fields and
- * sources for block_big in {128, 256} and hsmall in {0, 11, 15, 19, 22, 24, 27}, keeps the
+ * sources for block_big in {128, 256} and hsmall in {0, 11, 15, 19, 22, 24, 27, 30}, keeps the
  * fastest and returns it in *h_block, *h_hsmall (either may be NULL).  With a
  * cache file (may be NULL), a line "<workload key> <block> <hsmall>" whose key
  * (box sizes, source count and radius distribution) matches is used without

@@ -224,10 +224,11 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
       g.stats.launches += 1;
     }
     if (split < n_items) {
-      // warp mode: CTAs of 8 or 4 warps, whichever keeps more warps resident (a
-      // warp's shared memory grows with its layer capacity; smaller CTAs pack better)
+      // warp mode: CTAs of 1..8 warps, whichever keeps the most warps resident (a
+      // warp's shared memory grows with its layer capacity, and every CTA also
+      // reserves some; ties go to the larger CTA)
       int wpb = 8, maxg = 0;
-      for (int cand : {8, 4}) {
+      for (int cand = 8; cand >= 1; --cand) {
         const int mg = faces_max_grid(32, faces_smem_bytes(hsm, 32) * cand, cand);
         if (mg * cand > maxg * wpb) {
           maxg = mg;
@@ -787,7 +788,7 @@ rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_
   double* gam = nullptr;
   TRY(cudaMalloc(&gam, g.ncell * sizeof(double)));
   const int blocks[] = {128, 256};
-  const int hss[] = {0, 11, 15, 19, 22, 24, 27};
+  const int hss[] = {0, 11, 15, 19, 22, 24, 27, 30};
   float best = 1e30f;
   int bb = g.block_big, bh = g.hsmall;
   cudaEvent_t e0 = nullptr, e1 = nullptr;

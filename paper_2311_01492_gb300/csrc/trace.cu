@@ -279,8 +279,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_trace_faces(TraceArgs a
 
 // Warp mode: every warp traces its own items (small sources), with its own
 // slice of shared memory and warp-level synchronisation only.
-template <int WPB, bool COLDENS>
-__global__ void __launch_bounds__(WPB * 32, 1024 / (WPB * 32)) k_trace_faces_warp(TraceArgs a) {
+// The CTA holds 1..8 warps (blockDim.x / 32), chosen at launch so that the most
+// warps stay resident for the shared memory one warp needs.
+template <bool COLDENS>
+__global__ void __launch_bounds__(256, 4) k_trace_faces_warp(TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (a.skip && *a.skip) return;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -302,15 +304,12 @@ __global__ void __launch_bounds__(WPB * 32, 1024 / (WPB * 32)) k_trace_faces_war
 }
 
 // Kernel variant for (block, warps per CTA, coldens); block 32 = warp mode with
-// wpb warps per CTA (4 or 8).  Null if not instantiated.
+// wpb warps per CTA (1..8).  Null if not instantiated.
 static const void* face_kernel(int block, int wpb, bool coldens) {
   switch (block) {
     case 32:
-      if (wpb == 4) return coldens ? (const void*)k_trace_faces_warp<4, true>
-                                   : (const void*)k_trace_faces_warp<4, false>;
-      if (wpb == 8) return coldens ? (const void*)k_trace_faces_warp<8, true>
-                                   : (const void*)k_trace_faces_warp<8, false>;
-      return nullptr;
+      if (wpb < 1 || wpb > 8) return nullptr;
+      return coldens ? (const void*)k_trace_faces_warp<true> : (const void*)k_trace_faces_warp<false>;
     case 128: return coldens ? (const void*)k_trace_faces<128, true>
                              : (const void*)k_trace_faces<128, false>;
     case 256: return coldens ? (const void*)k_trace_faces<256, true>
