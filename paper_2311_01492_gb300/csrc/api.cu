@@ -109,6 +109,7 @@ static TraceArgs base_args(Grid& g) {
   a.rtab_hcap = g.rtab_hcap;
   a.rtab_slot = g.rtab_slot;
   a.rtab_max_r2 = g.rtab_max_r2;
+  a.neg_zero = -0.0;
   a.geo_mmax = g.geo_mmax;
   a.tab.g = g.gtab;
   a.tab.h = g.htab;

@@ -91,6 +91,7 @@ struct TraceArgs {
   const int* skip;       // if non-null and *skip != 0 the launch does nothing
   unsigned long long* rate_cells;  // number of rate evaluations (may be null)
   int early_exit;        // stop an item once a whole layer is opaque (rates only)
+  double neg_zero;       // -0.0 at run time: fma(x, y, -0.0) is x*y bit for bit, as a DFMA
   uint64_t exit_bits;    // bits of the opacity bound 2^E1 (1 + 2^-40)
   // Row tables of unclipped quadrant layers, one blob per (R^2 limit, m):
   // first flat index of rows 0..H+1 (ints) then the row of every flat index
