@@ -164,6 +164,22 @@ def test_precomputed_row_tables_are_built_for_unclipped_radii():
     g.close()
 
 
+def test_large_radii_wide_layers():
+    """R up to 70 cells in a 144^3 box: layer half-widths up to 49 (two CTAs per SM),
+    row tables of 16-bit-row layers, window not clipping; plus one source whose radius
+    exceeds the window (clipped tables built in the kernel)."""
+    n = 144
+    rng = np.random.default_rng(21)
+    nH = S.lognormal_field(n, 2e-4, sigma_ln=0.8, seed=21)
+    xHI = rng.uniform(0.0, 1e-4, (n, n, n))  # nearly ionised: rates far from the source
+    pos = np.array([[10, 130, 70], [72, 72, 72], [0, 0, 0]], np.int32)
+    R = np.array([70.0, 45.5, 90.0])
+    ndot = np.array([1e52, 3e51, 1e52])
+    w = dict(n=n, cell_cm=0.5 * S.MPC_CM, nH=nH, xHI=xHI, pos=pos, ndot=ndot, radius=R)
+    run_both(w, table("bb"), schedules=("batched",), cd_srcs=(0, 2), sched=(128, 0))
+    run_both(w, table("bb"), schedules=("batched",), cd_srcs=(1,), sched=(256, 27))
+
+
 def test_degenerate_sizes():
     # one-cell box, radius below one cell, zero rate, huge radius clipped by the window
     for n, R, nd in [(1, 5.0, 1e50), (8, 0.5, 1e50), (8, 100.0, 0.0), (2, 3.0, 1e49)]:
