@@ -109,46 +109,11 @@ __device__ __forceinline__ void group_sync() {
   if (GS == 32) __syncwarp(); else __syncthreads();
 }
 
-// Row table of one quadrant layer: rows a1 = 0..nrows-1 (|t1|), row a1 holds
-// a2 = 0..min(w, lim2) with w = min(H, floor(sqrt(rem - a1^2))).  rowpre[a1] is
-// the first flat index of row a1, rowpre[nrows] the layer size; rowof[t] the
-// row of flat index t.  Ends with the group synchronised.
-template <int GS>
-__device__ __forceinline__ void quad_rows(int rem, int H, int nrows, int lim2,
-                                          int* __restrict__ rowpre,
-                                          unsigned char* __restrict__ rowof, int gt) {
-  constexpr int NW = GS / 32;
-  const int lane = gt & 31, wid = gt >> 5;
-  if (wid == 0) {
-    const int per = (nrows + 31) >> 5;
-    const int rb = lane * per, re = min(nrows, rb + per);
-    int local = 0;
-    for (int r = rb; r < re; ++r) local += min(min(H, isqrt_i(rem - r * r)), lim2) + 1;
-    int incl = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    int run = incl - local;
-    for (int r = rb; r < re; ++r) {
-      rowpre[r] = run;
-      run += min(min(H, isqrt_i(rem - r * r)), lim2) + 1;
-    }
-    if (lane == 31) rowpre[nrows] = incl;
-  }
-  group_sync<GS>();
-  for (int r = wid; r < nrows; r += NW) {
-    const int p0 = rowpre[r], len = rowpre[r + 1] - p0;
-    for (int c = lane; c < len; c += 32) rowof[p0 + c] = (unsigned char)r;
-  }
-  group_sync<GS>();
-}
-
 // Row tables of one quadrant layer built by a single warp (lane = 0..31), no
-// synchronisation: rowpre[a1] = first flat index of row a1, rowpre[nrows] =
-// layer size, rowof[t] = row of flat index t.  Each lane handles a contiguous
-// block of rows, so its rowof writes are one contiguous range.
+// synchronisation.  Rows a1 = 0..nrows-1 (|t1|); row a1 holds a2 = 0..min(w, lim2)
+// with w = min(H, floor(sqrt(rem - a1^2))).  rowpre[a1] = first flat index of row
+// a1, rowpre[nrows] = layer size, rowof[t] = row of flat index t.  Each lane
+// handles a contiguous block of rows, so its rowof writes are one contiguous range.
 __device__ __forceinline__ void quad_rows_warp(int rem, int H, int nrows, int lim2,
                                                int* __restrict__ rowpre,
                                                unsigned char* __restrict__ rowof, int lane) {
