@@ -55,6 +55,9 @@ def parse():
                     help="with --no-autotune: threads per CTA of the large-source kernel")
     ap.add_argument("--hsmall", type=int, default=19,
                     help="with --no-autotune: largest layer half-width traced by single warps")
+    ap.add_argument("--hface", type=int, default=13,
+                    help="with --no-autotune: largest layer half-width traced by packed warps "
+                         "(four quadrants of a face per warp; 0 = off)")
     ap.add_argument("--adjoint-src", type=int, default=100_000,
                     help="sources of the gradient-throughput measurement (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -234,7 +237,7 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     g.set_sources(pos_d, ndot_d, R_d)
     if args.no_autotune:
-        tuned = (args.block, args.hsmall)
+        tuned = (args.block, args.hsmall, args.hface)
         g.set_schedule(*tuned)
     else:
         tuned = g.autotune(os.path.join(ROOT, "gpurun_out", "autotune_cache.txt")
@@ -457,8 +460,8 @@ def main():
             "config": {"workload": w["name"], "n": n, "box_mpc": args.box_mpc,
                        "nsrc": len(w["ndot"]), "radius_cells": "5-50 (R=5(Ndot/1e50)^0.2)",
                        "schedule": "batched (persistent, 24 face-quadrant items/source, LPT "
-                                   "queue; autotuned CTA %d threads, warp mode for layer "
-                                   "half-width <= %d)" % tuned,
+                                   "queue; CTA %d threads, warp mode for layer half-width "
+                                   "<= %d, four quadrants per warp for <= %d)" % tuned,
                        "step": "ingest + dtau + trace + chemistry",
                        "l2": "512 MB write between steps; fields 3 x 125 MB > L2",
                        "per_rank": "independent box per rank (weak scaling)"},

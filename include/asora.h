@@ -201,18 +201,22 @@ typedef struct {
 
 /* Schedule of RT_SCHED_BATCHED: items of sources whose largest layer half-width
  * exceeds hsmall are traced by CTAs of block_big threads (128 or 256), the
- * others by single warps (hsmall 0..32; 0 = CTAs only).  Defaults 128, 19;
+ * others by single warps (hsmall 0..32; 0 = CTAs only); of those, sources whose
+ * largest layer half-width is at most hface (0..20; 0 = off) are traced by warps
+ * that take the four quadrants of a face together.  Defaults 128, 19, 13;
  * results do not depend on the choice. */
-rt_status rt_set_schedule(rt_grid_t g, int block_big, int hsmall);
+rt_status rt_set_schedule(rt_grid_t g, int block_big, int hsmall, int hface);
 
 /* Autotuner of RT_SCHED_BATCHED: times rt_raytrace on the registered fields and
- * sources for block_big in {128, 256} and hsmall in {0, 11, 15, 19, 22, 24, 27, 30}, keeps the
- * fastest and returns it in *h_block, *h_hsmall (either may be NULL).  With a
- * cache file (may be NULL), a line "<workload key> <block> <hsmall>" whose key
- * (box sizes, source count and radius distribution) matches is used without
- * timing, and a new result is appended.  Synchronises; allocates one temporary
- * rate field. */
-rt_status rt_autotune(rt_grid_t g, const char* cache_path, int* h_block, int* h_hsmall);
+ * sources for block_big in {128, 256} x hsmall in {0, 11, 15, 19, 22, 24, 27, 30}
+ * (packed warps off), then hface in {9, 11, 13, 15, 17, 19} at the fastest pair; keeps
+ * the fastest and returns it in *h_block, *h_hsmall, *h_hface (any may be NULL).
+ * With a cache file (may be NULL), a line "<workload key> <block> <hsmall>
+ * <hface>" whose key (box sizes, source count and radius distribution) matches
+ * is used without timing, and a new result is appended.  Synchronises; allocates
+ * one temporary rate field. */
+rt_status rt_autotune(rt_grid_t g, const char* cache_path, int* h_block, int* h_hsmall,
+                      int* h_hface);
 
 /* Statistics of the last trace (synchronises the grid's stream). */
 rt_status rt_get_stats(rt_grid_t g, rt_stats* out);

@@ -54,10 +54,10 @@ SIGNATURES = {
     "rt_chemistry_step": (_I, [_P, _P, _P, _P, _D, _D, _D, _D, _P, _P, _P]),
     "rt_iterate": (_I, [_P, _P, _D, _D, _D, _I, _D, _D, _I, _P, C.POINTER(_I)]),
     "rt_get_stats": (_I, [_P, C.POINTER(rt_stats)]),
-    "rt_set_schedule": (_I, [_P, _I, _I]),
+    "rt_set_schedule": (_I, [_P, _I, _I, _I]),
     "rt_raytrace_backward": (_I, [_P, _P, _P, _P]),
     "rt_set_adjoint_mode": (_I, [_P, _I]),
-    "rt_autotune": (_I, [_P, C.c_char_p, C.POINTER(_I), C.POINTER(_I)]),
+    "rt_autotune": (_I, [_P, C.c_char_p, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "rt_grid_destroy": (None, [_P]),
     "rt_shell_enumerate": (_I, [_I, _P]),
     "rt_kernel_launch_count": (C.c_longlong, []),

@@ -201,17 +201,19 @@ class Grid:
         L.check(self._lib.rt_set_adjoint_mode(self._h, int(bool(stop_at_opaque))),
                 "rt_set_adjoint_mode")
 
-    def set_schedule(self, block_big=128, hsmall=19):
-        L.check(self._lib.rt_set_schedule(self._h, int(block_big), int(hsmall)),
+    def set_schedule(self, block_big=128, hsmall=19, hface=13):
+        """Batched schedule: CTA size, warp-mode threshold, packed-warp threshold."""
+        L.check(self._lib.rt_set_schedule(self._h, int(block_big), int(hsmall), int(hface)),
                 "rt_set_schedule")
 
     def autotune(self, cache_path=None):
-        """Pick the batched schedule (CTA size, warp-mode threshold) by timing."""
-        b, hs = C.c_int(0), C.c_int(0)
+        """Pick the batched schedule by timing; returns (block_big, hsmall, hface)."""
+        b, hs, hf = C.c_int(0), C.c_int(0), C.c_int(0)
         L.check(self._lib.rt_autotune(self._h, None if cache_path is None else
-                                      str(cache_path).encode(), C.byref(b), C.byref(hs)),
+                                      str(cache_path).encode(), C.byref(b), C.byref(hs),
+                                      C.byref(hf)),
                 "rt_autotune")
-        return b.value, hs.value
+        return b.value, hs.value, hf.value
 
     def stats(self):
         s = L.rt_stats()

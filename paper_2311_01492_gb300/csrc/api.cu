@@ -149,9 +149,11 @@ static rt_status check_ready(Grid& g, const char* who) {
 
 // Trace all sources, adding rates into `gamma` (already zeroed) or writing one
 // source's column densities.  `items`/`n_items` select the work.
+// single_r2 >= 0: the items are the 24 of one source with that R^2 limit (else
+// the grid's LPT list, whose limits are g.r2_sorted_h).
 static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* items, int n_items,
                            int schedule, int nsrc_plain, const int* skip = nullptr,
-                           bool early_exit = false) {
+                           bool early_exit = false, int single_r2 = -1) {
   TraceArgs a = base_args(g);
   a.gamma = gamma;
   a.coldens = coldens;
@@ -187,25 +189,57 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
       return fail(RT_ERR_INVALID, "rt_raytrace: the batched schedule needs boxes of at most "
                                   "1290^3 cells (32-bit offsets); use RT_SCHED_PLAIN");
     // Batched: items of large sources are traced by whole CTAs, items whose
-    // layers fit g.hsmall by single warps (items are in LPT order, so the
-    // warp-mode items are a suffix).
-    const int hbig = face_hcap(g.max_r2, g.nmax);
-    int split = n_items, hsm = 0;
-    if (items == g.items && g.hsmall > 0 && !g.r2_sorted_h.empty()) {
-      int lo = 0, hi = (int)g.r2_sorted_h.size();  // first p with face_hcap(r2[p]) <= hsmall
+    // layers fit g.hsmall by single warps, and items whose layers fit g.hface by
+    // single warps that take the four quadrants of a face together.  Items come
+    // in LPT order (24 per source, r2 non-increasing), so each mode gets a
+    // contiguous range of sources: [0, pw) CTAs, [pw, p4) warps, [p4, ns) packed.
+    const int* r2s = single_r2 >= 0 ? &single_r2 : g.r2_sorted_h.data();
+    const int ns = n_items / 24;
+    auto first_fitting = [&](int hlim) {  // first source whose layers fit hlim (ns: none)
+      if (hlim <= 0) return ns;
+      int lo = 0, hi = ns;
       while (lo < hi) {
         const int mid = (lo + hi) / 2;
-        if (face_hcap(g.r2_sorted_h[mid], g.nmax) <= g.hsmall) hi = mid; else lo = mid + 1;
+        if (face_hcap(r2s[mid], g.nmax) <= hlim) hi = mid; else lo = mid + 1;
       }
-      if (lo < (int)g.r2_sorted_h.size()) {
-        split = std::min(n_items, 24 * lo);
-        hsm = face_hcap(g.r2_sorted_h[lo], g.nmax);
-      }
-    }
-    TRY(cudaMemsetAsync(g.queue, 0, 2 * sizeof(int), g.stream));
+      return lo;
+    };
+    const int pw = first_fitting(g.hsmall);
+    const int p4 = std::max(pw, first_fitting(g.hface));
+    const int hbig = face_hcap(r2s[0], g.nmax);
+    TRY(cudaMemsetAsync(g.queue, 0, 3 * sizeof(int), g.stream));
     a.items = items;
     g.stats.launches = 0;
-    if (split > 0) {
+    // warp modes: CTAs of 1..8 warps, whichever keeps the most warps resident (a
+    // warp's shared memory grows with its layer capacity, and every CTA also
+    // reserves some; ties go to the larger CTA)
+    auto warp_launch = [&](int mode, int hcap, int item_begin, int item_end, int* queue) {
+      int wpb = 8, maxg = 0;
+      for (int cand = 8; cand >= 1; --cand) {
+        const int mg = faces_max_grid(mode, faces_smem_bytes(hcap, mode) * cand, cand);
+        if (mg * cand > maxg * wpb) {
+          maxg = mg;
+          wpb = cand;
+        }
+      }
+      if (maxg <= 0) return fail(RT_ERR_CUDA, "rt_raytrace: no occupancy for a warp face kernel");
+      g.warps_per_block = wpb;
+      TraceArgs b = a;
+      b.hcap = hcap;
+      b.item_begin = item_begin;
+      b.n_items = item_end;
+      b.queue = queue;
+      const int nitem = item_end - item_begin;
+      const int grid = std::max(1, std::min((nitem + wpb - 1) / wpb, maxg));
+      TRY(launch_trace_faces(g, b, mode, grid, faces_smem_bytes(hcap, mode) * wpb, wpb));
+      g.stats.launches += 1;
+      if (g.stats.launches == 1) {
+        g.stats.block = 32 * wpb;
+        g.stats.grid = grid;
+      }
+      return RT_OK;
+    };
+    if (pw > 0) {
       const int block = g.block_big;
       const size_t smem = faces_smem_bytes(hbig, block);
       if (smem > 227 * 1024)
@@ -216,42 +250,21 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
       TraceArgs b = a;
       b.hcap = hbig;
       b.item_begin = 0;
-      b.n_items = split;
+      b.n_items = 24 * pw;
       b.queue = g.queue;
-      const int grid = std::max(1, std::min(split, maxg));
+      const int grid = std::max(1, std::min(24 * pw, maxg));
       TRY(launch_trace_faces(g, b, block, grid, smem));
       g.stats.block = block;
       g.stats.grid = grid;
       g.stats.launches += 1;
     }
-    if (split < n_items) {
-      // warp mode: CTAs of 1..8 warps, whichever keeps the most warps resident (a
-      // warp's shared memory grows with its layer capacity, and every CTA also
-      // reserves some; ties go to the larger CTA)
-      int wpb = 8, maxg = 0;
-      for (int cand = 8; cand >= 1; --cand) {
-        const int mg = faces_max_grid(32, faces_smem_bytes(hsm, 32) * cand, cand);
-        if (mg * cand > maxg * wpb) {
-          maxg = mg;
-          wpb = cand;
-        }
-      }
-      g.warps_per_block = wpb;
-      const size_t smem = faces_smem_bytes(hsm, 32) * wpb;
-      if (maxg <= 0) return fail(RT_ERR_CUDA, "rt_raytrace: no occupancy for the warp face kernel");
-      TraceArgs b = a;
-      b.hcap = hsm;
-      b.item_begin = split;
-      b.n_items = n_items;
-      b.queue = g.queue + 1;
-      const int nitem = n_items - split;
-      const int grid = std::max(1, std::min((nitem + wpb - 1) / wpb, maxg));
-      TRY(launch_trace_faces(g, b, 32, grid, smem, wpb));
-      g.stats.launches += 1;
-      if (split == 0) {
-        g.stats.block = 32;
-        g.stats.grid = grid;
-      }
+    if (p4 > pw) {
+      rt_status ws = warp_launch(32, face_hcap(r2s[pw], g.nmax), 24 * pw, 24 * p4, g.queue + 1);
+      if (ws != RT_OK) return ws;
+    }
+    if (ns > p4) {  // packed: face items it -> items[4 it]
+      rt_status ws = warp_launch(4, face_hcap(r2s[p4], g.nmax), 6 * p4, 6 * ns, g.queue + 2);
+      if (ws != RT_OK) return ws;
     }
     g.stats.items = n_items;
   }
@@ -496,7 +509,8 @@ rt_status rt_raytrace_source_coldens(rt_grid_t h, int src, double* d_coldens, in
     TRY(cudaMemcpyAsync(g.queue + 8, hitems, sizeof(int), cudaMemcpyHostToDevice, g.stream));
     st = run_trace(g, nullptr, d_coldens, g.queue + 8, 1, RT_SCHED_PLAIN, 1);
   } else {
-    st = run_trace(g, nullptr, d_coldens, g.queue + 8, 24, RT_SCHED_BATCHED, 0);
+    st = run_trace(g, nullptr, d_coldens, g.queue + 8, 24, RT_SCHED_BATCHED, 0, nullptr, false,
+                   g.r2_sorted_h[p]);
   }
   if (st != RT_OK) return st;
   TRY(cudaStreamSynchronize(g.stream));  // hitems is a stack buffer
@@ -740,15 +754,18 @@ rt_status rt_set_adjoint_mode(rt_grid_t h, int stop_at_opaque) {
   return RT_OK;
 }
 
-rt_status rt_set_schedule(rt_grid_t h, int block_big, int hsmall) {
+rt_status rt_set_schedule(rt_grid_t h, int block_big, int hsmall, int hface) {
   if (!h) return fail(RT_ERR_INVALID, "rt_set_schedule: null grid");
   if (block_big != 128 && block_big != 256)
     return fail(RT_ERR_INVALID, "rt_set_schedule: block must be 128 or 256");
   if (hsmall < 0 || hsmall > 32)
     return fail(RT_ERR_INVALID, "rt_set_schedule: hsmall must be 0..32");
+  if (hface < 0 || hface > 20)
+    return fail(RT_ERR_INVALID, "rt_set_schedule: hface must be 0..20");
   Grid& g = *reinterpret_cast<Grid*>(h);
   g.block_big = block_big;
   g.hsmall = hsmall;
+  g.hface = hface;
   return RT_OK;
 }
 
@@ -763,11 +780,17 @@ static std::string tune_key(const Grid& g) {
   return k.str();
 }
 
-rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_hsmall) {
+rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_hsmall,
+                      int* h_hface) {
   if (!h) return fail(RT_ERR_INVALID, "rt_autotune: null grid");
   Grid& g = *reinterpret_cast<Grid*>(h);
   rt_status st = check_ready(g, "rt_autotune");
   if (st != RT_OK) return st;
+  auto report = [&]() {
+    if (h_block) *h_block = g.block_big;
+    if (h_hsmall) *h_hsmall = g.hsmall;
+    if (h_hface) *h_hface = g.hface;
+  };
   const std::string key = tune_key(g);
   if (cache_path) {
     std::ifstream in(cache_path);
@@ -775,56 +798,79 @@ rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_
     while (std::getline(in, line)) {
       std::istringstream ls(line);
       std::string k;
-      int b = 0, hs = -1;
-      if ((ls >> k >> b >> hs) && k == key && (b == 128 || b == 256) && hs >= 0 && hs <= 32) {
+      int b = 0, hs = -1, hf = -1;
+      if ((ls >> k >> b >> hs >> hf) && k == key && (b == 128 || b == 256) && hs >= 0 &&
+          hs <= 32 && hf >= 0 && hf <= 20) {
         g.block_big = b;
         g.hsmall = hs;
-        if (h_block) *h_block = b;
-        if (h_hsmall) *h_hsmall = hs;
+        g.hface = hf;
+        report();
         return RT_OK;
       }
     }
   }
-  if (g.nsrc == 0) return RT_OK;
+  if (g.nsrc == 0) {
+    report();
+    return RT_OK;
+  }
   double* gam = nullptr;
   TRY(cudaMalloc(&gam, g.ncell * sizeof(double)));
-  const int blocks[] = {128, 256};
-  const int hss[] = {0, 11, 15, 19, 22, 24, 27, 30};
-  float best = 1e30f;
-  int bb = g.block_big, bh = g.hsmall;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  // time of one batched trace in the current configuration (second of two runs)
+  auto timed = [&](float& t) {
+    for (int rep = 0; rep < 2 && st == RT_OK; ++rep) {
+      cudaEventRecord(e0, g.stream);
+      st = rt_raytrace(h, gam, RT_SCHED_BATCHED);
+      cudaEventRecord(e1, g.stream);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&t, e0, e1);
+    }
+    return st == RT_OK;
+  };
+  // stage 1: CTA size x warp-mode threshold (packed warps off); stage 2: the
+  // packed-warp threshold at the chosen pair
+  const int blocks[] = {128, 256};
+  const int hss[] = {0, 11, 15, 19, 22, 24, 27, 30};
+  const int hfs[] = {9, 11, 13, 15, 17, 19};
+  float best = 1e30f;
+  int bb = g.block_big, bh = g.hsmall, bf = 0;
+  g.hface = 0;
   for (int b : blocks)
     for (int hs : hss) {
+      if (st != RT_OK) break;
       g.block_big = b;
       g.hsmall = hs;
       float t = 0.f;
-      for (int rep = 0; rep < 2 && st == RT_OK; ++rep) {
-        cudaEventRecord(e0, g.stream);
-        st = rt_raytrace(h, gam, RT_SCHED_BATCHED);
-        cudaEventRecord(e1, g.stream);
-        cudaEventSynchronize(e1);
-        cudaEventElapsedTime(&t, e0, e1);
-      }
-      if (st != RT_OK) break;
+      if (!timed(t)) break;
       if (t < best) {
         best = t;
         bb = b;
         bh = hs;
       }
     }
+  g.block_big = bb;
+  g.hsmall = bh;
+  for (int hf : hfs) {
+    if (st != RT_OK || bh == 0) break;
+    g.hface = hf;
+    float t = 0.f;
+    if (!timed(t)) break;
+    if (t < best) {
+      best = t;
+      bf = hf;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(gam);
   if (st != RT_OK) return st;
-  g.block_big = bb;
-  g.hsmall = bh;
-  if (h_block) *h_block = bb;
-  if (h_hsmall) *h_hsmall = bh;
+  g.hface = bf;
+  report();
   if (cache_path) {
     std::ofstream out(cache_path, std::ios::app);
-    out << key << " " << bb << " " << bh << "\n";
+    out << key << " " << bb << " " << bh << " " << bf << "\n";
   }
   return RT_OK;
 }

@@ -87,6 +87,14 @@ __host__ __device__ inline size_t group_smem_bytes(int h, bool warp) {
   return layer_bytes(h, warp) + 2 * (size_t)row_slot_bytes(h);
 }
 
+// Shared memory of one warp tracing the four quadrants of a face together:
+// four in-place layers of (h+1)^2 doubles, then two row-table slots (shared by
+// the quadrants).  Also holds the single-quadrant layout of group_smem_bytes.
+__host__ __device__ inline size_t face4_smem_bytes(int h) {
+  const size_t cap = (size_t)(h + 1) * (h + 1);
+  return ((4 * cap * sizeof(double) + 15) & ~(size_t)15) + 2 * (size_t)row_slot_bytes(h);
+}
+
 // Asynchronous copy of a precomputed row-table blob (16-byte aligned, size a
 // multiple of 16) into a shared-memory slot by the GS threads of a group; the
 // copies complete at the next cp_async_wait_all of each issuing thread.

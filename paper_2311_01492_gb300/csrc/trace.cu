@@ -40,7 +40,9 @@
 namespace asora {
 
 // ----------------------------------------------------------- face kernels
-size_t faces_smem_bytes(int hcap, int block) { return group_smem_bytes(hcap, block == 32); }
+size_t faces_smem_bytes(int hcap, int block) {
+  return block == 4 ? face4_smem_bytes(hcap) : group_smem_bytes(hcap, block == 32);
+}
 
 // Trace one (source, face, quadrant) item with a group of GS threads (gt =
 // thread index in the group).  Within a face, a cell's interpolants never
@@ -253,6 +255,163 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
   }
 }
 
+// Packed warp mode: one warp traces the four quadrants of a face together (small
+// sources).  Lane u of a round takes cell t = u >> 2 of quadrant k = u & 3, so the
+// four lanes of a cell position share its row-table and geometry loads, and a
+// round holds four times as many cells as in quadrant warp mode.  Each quadrant
+// keeps its own in-place layer buffer; the descending order and the
+// read-before-write rounds of trace_face_item hold per quadrant (a round starts
+// at u = 3 mod 4, so each lane keeps one quadrant).  Items whose window clips a
+// layer (no precomputed tables) are traced quadrant by quadrant instead.
+template <bool COLDENS>
+__device__ __forceinline__ void trace_face4_warp(const TraceArgs& a, const int item, const int lane,
+                                                 unsigned char* __restrict__ sm, const int h,
+                                                 unsigned& nrate) {
+  const int s = item >> 5, f = (item >> 2) & 7;
+  const SrcDev S = a.src[s];
+  const BoxDev B = a.boxes[S.box];
+  const int R2 = a.r2lim[s];
+  const int* toff = nullptr;
+  if (R2 <= a.rtab_max_r2) {
+    const int sl = a.rtab_slot[R2];
+    if (sl >= 0 && a.rtab_hcap[sl] <= min(B.whi, -B.wlo)) toff = a.rtab_off + a.rtab_first[sl] - 1;
+  }
+  if (!toff) {
+    for (int k = 0; k < 4; ++k) {
+      trace_face_item<32, COLDENS>(a, (item & ~3) | k, lane, sm, h, nrate);
+      __syncwarp();
+    }
+    return;
+  }
+  const int cap = (h + 1) * (h + 1), W = h + 1;
+  const int TS = row_slot_bytes(h);
+  unsigned char* tab2 = sm + ((4 * (size_t)cap * sizeof(double) + 15) & ~(size_t)15);  // [2][TS]
+  const int N = B.n;
+  const double nd = a.ndot[s];
+  const int d = f >> 1;
+  const int sg = (f & 1) ? -1 : 1;
+  int Lmax = sg > 0 ? B.whi : -B.wlo;
+  Lmax = min(Lmax, isqrt_i(R2));
+  const int64_t scell = B.off + ((int64_t)S.i * N + S.j) * N + S.k;
+  const double dts = a.dtau[scell];
+
+  if (f == 4 && lane == 0) {  // the source cell (q = 0), once per source
+    const double tout = 0.5 * dts;
+    if (COLDENS) {
+      a.coldens[scell] = tout / a.sigma0;
+    } else {
+      double dG;
+      if (bits_of(tout) <= bits_of(a.tau_lim))
+        dG = nd * (tab_eval(a.tab.h, a.tab, 0.0) * (0.5 * B.thin_fac));
+      else
+        dG = nd * ((tab_eval(a.tab.g, a.tab, 0.0) - tab_eval(a.tab.g, a.tab, tout)) *
+                   B.inv_cell3 * a.invn[scell]);
+      ++nrate;
+      if (dG != 0.0) atomicAdd(&a.gamma[scell], dG);
+    }
+  }
+
+  // axes and layouts as in trace_face_item
+  const int NN = N * N;
+  const int c1 = d == 0 ? S.j : S.i;
+  const int c2 = d == 2 ? S.j : S.k;
+  const int cd = d == 0 ? S.i : (d == 1 ? S.j : S.k);
+  const int m1 = d == 1 ? NN : N;
+  const int md = d == 1 ? N : NN;
+  const double* __restrict__ fld = (d == 2 ? a.dtauT : a.dtau) + B.off;
+
+  const int k = 3 - (lane & 3);  // this lane's quadrant for every round
+  const int q1 = (k & 1) ? -1 : 1, q2 = (k & 2) ? -1 : 1;
+  double* qb = reinterpret_cast<double*>(sm) + k * cap;
+  int Hp = 0;
+  const bool exit_ok = !COLDENS && a.early_exit;
+  if (Lmax >= 1 && min(1, isqrt_i(R2 - 1)) <= h) {
+    stage_rows<32>(a.rtab + toff[1], toff[2] - toff[1], tab2 + TS, lane);
+    cp_async_wait_all();
+  }
+  __syncwarp();
+  for (int m = 1; m <= Lmax; ++m) {
+    const int rem = R2 - m * m;
+    const int H = min(m, isqrt_i(rem));
+    if (H > h || m > a.geo_mmax) {
+      if (lane == 0) atomicOr(a.err, H > h ? ERR_LAYER_CAP : ERR_GEO);
+      break;
+    }
+    const int nrows = H + 1;
+    const int* rowpre = reinterpret_cast<const int*>(tab2 + (m & 1) * TS);
+    const unsigned char* rowof = reinterpret_cast<const unsigned char*>(rowpre + nrows + 1);
+    const int total = rowpre[nrows];
+    int Hn = 0;
+    if (m < Lmax) {
+      Hn = min(m + 1, isqrt_i(R2 - (m + 1) * (m + 1)));
+      if (Hn <= h)
+        stage_rows<32>(a.rtab + toff[m + 1], toff[m + 2] - toff[m + 1], tab2 + ((m + 1) & 1) * TS,
+                       lane);
+    }
+    const int lc = wrapc(cd + sg * m, N);
+    const int lay = lc * md;
+    const GeoRow* __restrict__ grow = a.georow + georow_index(m, 0, 0);
+    const int gbase = (int)geo_index(m, 0, 0);
+    bool opaque = true;
+    for (int t0 = 4 * total - 1; t0 >= 0; t0 -= 32) {
+      const int u = t0 - lane;  // u = 4 t + k; lanes below 0 recompute cell 0, write nothing
+      const int t = max(u, 0) >> 2;
+      const int a1 = rowof[t];
+      const int a2 = t - rowpre[a1];
+      const int x1 = wrapc(c1 + q1 * a1, N), x2 = wrapc(c2 + q2 * a2, N);
+      const int gidx = lay + x1 * m1 + x2;
+      const double dtp = __ldg(&fld[gidx]);
+      const GeoRow* gr = grow + a1 * (m + 1) + a2;
+      const double2 wv0 = __ldg(reinterpret_cast<const double2*>(gr));      // w1, w2
+      const double2 wv1 = __ldg(reinterpret_cast<const double2*>(gr) + 1);  // w3, w4
+      const double ds = __ldg(&gr->ds);
+      double tin;
+      if (m == 1) {
+        tin = (0.5 * dts) * ds;
+      } else {
+        const double w1 = wv0.x, w2 = wv0.y, w3 = wv1.x, w4 = wv1.y;
+        const int b1 = min(a1, Hp), b2 = min(a1 - (a1 > 0), Hp);
+        const int e1 = min(a2, Hp), e2 = min(a2 - (a2 > 0), Hp);
+        const double v1 = qb[b1 * W + e1];
+        const double v2 = qb[b2 * W + e1];
+        const double v3 = qb[b1 * W + e2];
+        const double v4 = qb[b2 * W + e2];
+        tin = fma(w4, v4, fma(w3, v3, fma(w2, v2, fma(w1, v1, a.neg_zero))));
+      }
+      const double tout = fma(dtp, ds, tin);
+      __syncwarp();  // every lane has read layer m-1 before any lane writes
+      if (u < 0) continue;
+      qb[a1 * W + a2] = tout;
+      opaque = opaque && bits_of(tout) >= a.exit_bits;
+      const bool own = ((d == 2) || (d == 1 ? a2 < m : (a1 < m && a2 < m))) &&
+                       (a1 > 0 || q1 > 0) && (a2 > 0 || q2 > 0);
+      if (!own) continue;
+      if (COLDENS || bits_of(tin) < a.tab.tau_max_bits) {
+        const int64_t cell = B.off + (d == 2 ? (x1 * N + x2) * N + lc : gidx);
+        if (COLDENS) {
+          a.coldens[cell] = tout / a.sigma0;
+        } else {
+          const GeoEntry* ge = &a.geo[gbase + ((max(a1, a2) * (max(a1, a2) + 1)) >> 1) + min(a1, a2)];
+          const double dcell = dtp * ds;
+          const double dG = cell_rate(a, nd, tin, tout, dcell, __ldg(&ge->invv) * B.inv_cell3,
+                                      __ldg(&ge->thin) * B.thin_fac,
+                                      bits_of(dcell) <= bits_of(a.tau_lim) ? 0.0 : __ldg(&a.invn[cell]));
+          ++nrate;
+          if (dG != 0.0) atomicAdd(&a.gamma[cell], dG);
+        }
+      }
+    }
+    if (m < Lmax && Hn <= h) cp_async_wait_all();
+    if (exit_ok) {
+      __syncwarp();
+      if (__all_sync(0xffffffffu, opaque)) break;
+    } else {
+      __syncwarp();
+    }
+    Hp = H;
+  }
+}
+
 __device__ __forceinline__ void flush_rate_count(const TraceArgs& a, unsigned nrate) {
   if (!a.rate_cells) return;
   for (int o = 16; o > 0; o >>= 1) nrate += __shfl_down_sync(0xffffffffu, nrate, o);
@@ -306,6 +465,29 @@ __global__ void __launch_bounds__(256, 4) k_trace_faces_warp(TraceArgs a) {
   flush_rate_count(a, nrate);
 }
 
+// Packed warp mode kernel: items are faces (every 4th (face, quadrant) item).
+template <bool COLDENS>
+__global__ void __launch_bounds__(256, 4) k_trace_faces4_warp(TraceArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (a.skip && *a.skip) return;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* my = smem_raw + (size_t)wid * face4_smem_bytes(a.hcap);
+  const int cap4 = 4 * (a.hcap + 1) * (a.hcap + 1);
+  double* buf = reinterpret_cast<double*>(my);
+  for (int t = lane; t < cap4; t += 32) buf[t] = 0.0;
+  __syncwarp();
+  unsigned nrate = 0;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = a.item_begin + atomicAdd(a.queue, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= a.n_items) break;
+    trace_face4_warp<COLDENS>(a, a.items[4 * it], lane, my, a.hcap, nrate);
+    __syncwarp();
+  }
+  flush_rate_count(a, nrate);
+}
+
 // Kernel variant for (block, warps per CTA, coldens); block 32 = warp mode with
 // wpb warps per CTA (1..8).  Null if not instantiated.
 static const void* face_kernel(int block, int wpb, bool coldens) {
@@ -313,6 +495,9 @@ static const void* face_kernel(int block, int wpb, bool coldens) {
     case 32:
       if (wpb < 1 || wpb > 8) return nullptr;
       return coldens ? (const void*)k_trace_faces_warp<true> : (const void*)k_trace_faces_warp<false>;
+    case 4:  // packed warp mode (whole faces), wpb warps per CTA
+      if (wpb < 1 || wpb > 8) return nullptr;
+      return coldens ? (const void*)k_trace_faces4_warp<true> : (const void*)k_trace_faces4_warp<false>;
     case 128: return coldens ? (const void*)k_trace_faces<128, true>
                              : (const void*)k_trace_faces<128, false>;
     case 256: return coldens ? (const void*)k_trace_faces<256, true>
@@ -328,7 +513,7 @@ cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid,
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int threads = block == 32 ? wpb * 32 : block;
+  const int threads = (block == 32 || block == 4) ? wpb * 32 : block;
   TraceArgs arg = a;
   void* params[] = {&arg};
   e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), params, smem, g.stream);
@@ -342,7 +527,7 @@ int faces_max_grid(int block, size_t smem, int wpb) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const void* fn = face_kernel(block, wpb, false);
   if (!fn) return 0;
-  const int threads = block == 32 ? wpb * 32 : block;
+  const int threads = (block == 32 || block == 4) ? wpb * 32 : block;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
   if (e != cudaSuccess) return 0;

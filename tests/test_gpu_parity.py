@@ -130,15 +130,16 @@ def test_lognormal_boxes_many_sources(n, nsrc, rmax, seed):
     run_both(_random_box(n, nsrc, rmax, seed), table("bb"), cd_srcs=(0, 1, 3))
 
 
-# batched launch configurations (block_big, hsmall): CTAs only (hsmall 0), mixes
-# of CTA and warp items, and warps for every item that fits
-SCHEDS = [(128, 0), (256, 0), (128, 11), (256, 19), (128, 24)]
+# batched launch configurations (block_big, hsmall, hface): CTAs only (hsmall 0),
+# mixes of CTA, warp and packed-warp items, and warps for every item that fits
+SCHEDS = [(128, 0, 0), (256, 0, 0), (128, 11, 0), (256, 19, 13), (128, 24, 9), (128, 30, 20)]
 
 
 @pytest.mark.parametrize("sched", SCHEDS)
 def test_every_batched_configuration(sched):
     """Same column densities (bit for bit) and rates in every CTA/warp configuration,
-    including windows that clip the faces (even, odd and tiny boxes)."""
+    including windows that clip the faces (even, odd and tiny boxes).  Per-source
+    column densities take the same kernel as the source's items in the full trace."""
     for n, nsrc, rmax, seed in [(16, 20, 12.0, 1), (17, 30, 25.0, 2), (24, 40, 12.0, 3),
                                 (9, 5, 40.0, 4)]:
         run_both(_random_box(n, nsrc, rmax, seed), table("bb"), schedules=("batched", "early_exit"),
@@ -176,8 +177,8 @@ def test_large_radii_wide_layers():
     R = np.array([70.0, 45.5, 90.0])
     ndot = np.array([1e52, 3e51, 1e52])
     w = dict(n=n, cell_cm=0.5 * S.MPC_CM, nH=nH, xHI=xHI, pos=pos, ndot=ndot, radius=R)
-    run_both(w, table("bb"), schedules=("batched",), cd_srcs=(0, 2), sched=(128, 0))
-    run_both(w, table("bb"), schedules=("batched",), cd_srcs=(1,), sched=(256, 27))
+    run_both(w, table("bb"), schedules=("batched",), cd_srcs=(0, 2), sched=(128, 0, 0))
+    run_both(w, table("bb"), schedules=("batched",), cd_srcs=(1,), sched=(256, 27, 13))
 
 
 def test_degenerate_sizes():
