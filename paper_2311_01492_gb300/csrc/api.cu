@@ -252,7 +252,7 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
       b.item_begin = 0;
       b.n_items = 24 * pw;
       b.queue = g.queue;
-      const int grid = std::max(1, std::min(24 * pw, maxg));
+      const int grid = std::max(1, std::min(b.n_items, maxg));
       TRY(launch_trace_faces(g, b, block, grid, smem));
       g.stats.block = block;
       g.stats.grid = grid;

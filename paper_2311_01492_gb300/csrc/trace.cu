@@ -40,6 +40,7 @@
 namespace asora {
 
 // ----------------------------------------------------------- face kernels
+// block codes: 128/256 CTA mode, 32 warp mode, 4 packed warp mode
 size_t faces_smem_bytes(int hcap, int block) {
   return block == 4 ? face4_smem_bytes(hcap) : group_smem_bytes(hcap, block == 32);
 }
@@ -255,18 +256,35 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
   }
 }
 
-// Packed warp mode: one warp traces the four quadrants of a face together (small
-// sources).  Lane u of a round takes cell t = u >> 2 of quadrant k = u & 3, so the
-// four lanes of a cell position share its row-table and geometry loads, and a
-// round holds four times as many cells as in quadrant warp mode.  Each quadrant
-// keeps its own in-place layer buffer; the descending order and the
-// read-before-write rounds of trace_face_item hold per quadrant (a round starts
-// at u = 3 mod 4, so each lane keeps one quadrant).  Items whose window clips a
-// layer (no precomputed tables) are traced quadrant by quadrant instead.
-template <bool COLDENS>
-__device__ __forceinline__ void trace_face4_warp(const TraceArgs& a, const int item, const int lane,
-                                                 unsigned char* __restrict__ sm, const int h,
-                                                 unsigned& nrate) {
+// Packed mode: a group of GS threads (one warp, or a CTA) traces the four
+// quadrants of a face together.  Thread u of a round takes cell t = u >> 2 of
+// quadrant k = u & 3, so the four threads of a cell position share its row-table
+// and geometry loads, and a round holds four times as many cells as with one
+// quadrant.  Each quadrant keeps its own layer buffer, updated in place: the
+// cells are taken in descending order of u, GS at a time, every thread of the
+// group reads its interpolants before any thread writes (a barrier per round in
+// a CTA, a warp sync in a warp), and a cell reads only slots whose flat index is
+// not above its own -- later rounds cover smaller t, so no slot is rewritten
+// before it is read (a round starts at u = 3 mod 4, so every thread keeps one
+// quadrant).  Items whose window clips a layer (no precomputed tables) are traced
+// quadrant by quadrant instead.
+// The four quadrants of a face one after another (clipped windows), kept out of
+// line so that it does not weigh on the registers of the packed loop.
+template <int GS, bool COLDENS>
+__device__ __noinline__ void trace_face_by_quadrants(const TraceArgs& a, const int item,
+                                                     const int gt, unsigned char* sm, const int h,
+                                                     unsigned& nrate) {
+  for (int k = 0; k < 4; ++k) {
+    trace_face_item<GS, COLDENS>(a, (item & ~3) | k, gt, sm, h, nrate);
+    group_sync<GS>();
+  }
+}
+
+template <int GS, bool COLDENS>
+__device__ __forceinline__ void trace_face4(const TraceArgs& a, const int item, const int gt,
+                                            unsigned char* __restrict__ sm, const int h,
+                                            unsigned& nrate) {
+  const int lane = gt & 31;
   const int s = item >> 5, f = (item >> 2) & 7;
   const SrcDev S = a.src[s];
   const BoxDev B = a.boxes[S.box];
@@ -277,10 +295,7 @@ __device__ __forceinline__ void trace_face4_warp(const TraceArgs& a, const int i
     if (sl >= 0 && a.rtab_hcap[sl] <= min(B.whi, -B.wlo)) toff = a.rtab_off + a.rtab_first[sl] - 1;
   }
   if (!toff) {
-    for (int k = 0; k < 4; ++k) {
-      trace_face_item<32, COLDENS>(a, (item & ~3) | k, lane, sm, h, nrate);
-      __syncwarp();
-    }
+    trace_face_by_quadrants<GS, COLDENS>(a, item, gt, sm, h, nrate);
     return;
   }
   const int cap = (h + 1) * (h + 1), W = h + 1;
@@ -295,7 +310,7 @@ __device__ __forceinline__ void trace_face4_warp(const TraceArgs& a, const int i
   const int64_t scell = B.off + ((int64_t)S.i * N + S.j) * N + S.k;
   const double dts = a.dtau[scell];
 
-  if (f == 4 && lane == 0) {  // the source cell (q = 0), once per source
+  if (f == 4 && gt == 0) {  // the source cell (q = 0), once per source
     const double tout = 0.5 * dts;
     if (COLDENS) {
       a.coldens[scell] = tout / a.sigma0;
@@ -320,21 +335,21 @@ __device__ __forceinline__ void trace_face4_warp(const TraceArgs& a, const int i
   const int md = d == 1 ? N : NN;
   const double* __restrict__ fld = (d == 2 ? a.dtauT : a.dtau) + B.off;
 
-  const int k = 3 - (lane & 3);  // this lane's quadrant for every round
+  const int k = 3 - (gt & 3);  // this thread's quadrant for every round
   const int q1 = (k & 1) ? -1 : 1, q2 = (k & 2) ? -1 : 1;
   double* qb = reinterpret_cast<double*>(sm) + k * cap;
   int Hp = 0;
   const bool exit_ok = !COLDENS && a.early_exit;
   if (Lmax >= 1 && min(1, isqrt_i(R2 - 1)) <= h) {
-    stage_rows<32>(a.rtab + toff[1], toff[2] - toff[1], tab2 + TS, lane);
+    stage_rows<GS>(a.rtab + toff[1], toff[2] - toff[1], tab2 + TS, gt);
     cp_async_wait_all();
   }
-  __syncwarp();
+  group_sync<GS>();
   for (int m = 1; m <= Lmax; ++m) {
     const int rem = R2 - m * m;
     const int H = min(m, isqrt_i(rem));
     if (H > h || m > a.geo_mmax) {
-      if (lane == 0) atomicOr(a.err, H > h ? ERR_LAYER_CAP : ERR_GEO);
+      if (gt == 0) atomicOr(a.err, H > h ? ERR_LAYER_CAP : ERR_GEO);
       break;
     }
     const int nrows = H + 1;
@@ -345,16 +360,16 @@ __device__ __forceinline__ void trace_face4_warp(const TraceArgs& a, const int i
     if (m < Lmax) {
       Hn = min(m + 1, isqrt_i(R2 - (m + 1) * (m + 1)));
       if (Hn <= h)
-        stage_rows<32>(a.rtab + toff[m + 1], toff[m + 2] - toff[m + 1], tab2 + ((m + 1) & 1) * TS,
-                       lane);
+        stage_rows<GS>(a.rtab + toff[m + 1], toff[m + 2] - toff[m + 1], tab2 + ((m + 1) & 1) * TS,
+                       gt);
     }
     const int lc = wrapc(cd + sg * m, N);
     const int lay = lc * md;
     const GeoRow* __restrict__ grow = a.georow + georow_index(m, 0, 0);
     const int gbase = (int)geo_index(m, 0, 0);
     bool opaque = true;
-    for (int t0 = 4 * total - 1; t0 >= 0; t0 -= 32) {
-      const int u = t0 - lane;  // u = 4 t + k; lanes below 0 recompute cell 0, write nothing
+    for (int t0 = 4 * total - 1; t0 >= 0; t0 -= GS) {
+      const int u = t0 - gt;  // u = 4 t + k; threads below 0 recompute cell 0, write nothing
       const int t = max(u, 0) >> 2;
       const int a1 = rowof[t];
       const int a2 = t - rowpre[a1];
@@ -379,7 +394,7 @@ __device__ __forceinline__ void trace_face4_warp(const TraceArgs& a, const int i
         tin = fma(w4, v4, fma(w3, v3, fma(w2, v2, fma(w1, v1, a.neg_zero))));
       }
       const double tout = fma(dtp, ds, tin);
-      __syncwarp();  // every lane has read layer m-1 before any lane writes
+      group_sync<GS>();  // every thread has read layer m-1 before any thread writes
       if (u < 0) continue;
       qb[a1 * W + a2] = tout;
       opaque = opaque && bits_of(tout) >= a.exit_bits;
@@ -403,10 +418,16 @@ __device__ __forceinline__ void trace_face4_warp(const TraceArgs& a, const int i
     }
     if (m < Lmax && Hn <= h) cp_async_wait_all();
     if (exit_ok) {
-      __syncwarp();
-      if (__all_sync(0xffffffffu, opaque)) break;
+      bool all_opaque;
+      if (GS == 32) {
+        __syncwarp();
+        all_opaque = __all_sync(0xffffffffu, opaque);
+      } else {
+        all_opaque = __syncthreads_and(opaque) != 0;
+      }
+      if (all_opaque) break;
     } else {
-      __syncwarp();
+      group_sync<GS>();
     }
     Hp = H;
   }
@@ -482,14 +503,15 @@ __global__ void __launch_bounds__(256, 4) k_trace_faces4_warp(TraceArgs a) {
     if (lane == 0) it = a.item_begin + atomicAdd(a.queue, 1);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= a.n_items) break;
-    trace_face4_warp<COLDENS>(a, a.items[4 * it], lane, my, a.hcap, nrate);
+    trace_face4<32, COLDENS>(a, a.items[4 * it], lane, my, a.hcap, nrate);
     __syncwarp();
   }
   flush_rate_count(a, nrate);
 }
 
-// Kernel variant for (block, warps per CTA, coldens); block 32 = warp mode with
-// wpb warps per CTA (1..8).  Null if not instantiated.
+// Kernel variant for (block, warps per CTA, coldens): block 128/256 = CTA mode,
+// 32 = warp mode and 4 = packed warp mode with wpb warps per CTA (1..8).  Null if
+// not instantiated.
 static const void* face_kernel(int block, int wpb, bool coldens) {
   switch (block) {
     case 32:
