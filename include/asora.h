@@ -55,7 +55,7 @@ typedef struct {
 
 /* Trace schedules for rt_raytrace. */
 enum {
-  RT_SCHED_AUTO = 0,    /* batched, with the autotuned (or default) configuration           */
+  RT_SCHED_AUTO = 0,    /* batched (autotuned or default configuration), or plain if the autotuner found it faster */
   RT_SCHED_PLAIN = 1,   /* ASORA-style: one CTA per source, octahedral shells S_q in order   */
   RT_SCHED_BATCHED = 2, /* persistent work queue over (source, face, quadrant) items, LPT   */
   RT_SCHED_BATCHED_EXIT = 3 /* as BATCHED, but an item stops once a whole layer is opaque
@@ -211,10 +211,11 @@ rt_status rt_set_schedule(rt_grid_t g, int block_big, int hsmall, int hface);
  * sources for block_big in {128, 256} x hsmall in {0, 11, 15, 19, 22, 24, 27, 30}
  * (packed warps off), then hface in {9, 11, 13, 15, 17, 19} at the fastest pair; keeps
  * the fastest and returns it in *h_block, *h_hsmall, *h_hface (any may be NULL).
- * With a cache file (may be NULL), a line "<workload key> <block> <hsmall>
- * <hface>" whose key (box sizes, source count and radius distribution) matches
- * is used without timing, and a new result is appended.  Synchronises; allocates
- * one temporary rate field. */
+ * Finally times the plain (block-per-source) schedule once: RT_SCHED_AUTO takes
+ * whichever of the two is faster.  With a cache file (may be NULL), a line
+ * "<workload key> <block> <hsmall> <hface> <auto_plain>" whose key (box sizes,
+ * source count and radius distribution) matches is used without timing, and a
+ * new result is appended.  Synchronises; allocates one temporary rate field. */
 rt_status rt_autotune(rt_grid_t g, const char* cache_path, int* h_block, int* h_hsmall,
                       int* h_hface);
 

@@ -472,6 +472,7 @@ rt_status rt_raytrace(rt_grid_t h, double* d_gamma, int schedule) {
   TRY(launch_precompute(g));
   TRY(cudaMemsetAsync(d_gamma, 0, g.ncell * sizeof(double), g.stream));
   TRY(cudaEventRecord(g.ev[1], g.stream));
+  if (schedule == RT_SCHED_AUTO) schedule = g.auto_plain ? RT_SCHED_PLAIN : RT_SCHED_BATCHED;
   if (g.nsrc > 0) {
     if (schedule == RT_SCHED_PLAIN)
       st = run_trace(g, d_gamma, nullptr, nullptr, g.nsrc, RT_SCHED_PLAIN, g.nsrc);
@@ -798,12 +799,13 @@ rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_
     while (std::getline(in, line)) {
       std::istringstream ls(line);
       std::string k;
-      int b = 0, hs = -1, hf = -1;
-      if ((ls >> k >> b >> hs >> hf) && k == key && (b == 128 || b == 256) && hs >= 0 &&
-          hs <= 32 && hf >= 0 && hf <= 20) {
+      int b = 0, hs = -1, hf = -1, ap = -1;
+      if ((ls >> k >> b >> hs >> hf >> ap) && k == key && (b == 128 || b == 256) && hs >= 0 &&
+          hs <= 32 && hf >= 0 && hf <= 20 && (ap == 0 || ap == 1)) {
         g.block_big = b;
         g.hsmall = hs;
         g.hface = hf;
+        g.auto_plain = ap;
         report();
         return RT_OK;
       }
@@ -867,10 +869,28 @@ rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_
   cudaFree(gam);
   if (st != RT_OK) return st;
   g.hface = bf;
+  // stage 3: the paper's block-per-source schedule against the tuned batched one
+  // (RT_SCHED_AUTO then takes the faster)
+  if (st == RT_OK) {
+    float tp = 0.f;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    TRY(cudaMalloc(&gam, g.ncell * sizeof(double)));
+    cudaEventRecord(e0, g.stream);
+    st = rt_raytrace(h, gam, RT_SCHED_PLAIN);
+    cudaEventRecord(e1, g.stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&tp, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(gam);
+    if (st != RT_OK) return st;
+    g.auto_plain = tp < best ? 1 : 0;
+  }
   report();
   if (cache_path) {
     std::ofstream out(cache_path, std::ios::app);
-    out << key << " " << bb << " " << bh << " " << bf << "\n";
+    out << key << " " << bb << " " << bh << " " << bf << " " << g.auto_plain << "\n";
   }
   return RT_OK;
 }

@@ -199,6 +199,7 @@ struct Grid {
   int block_big = 128;      // threads per CTA for large-source items
   int hsmall = 19;          // items whose layers fit this half-width run one per warp
   int hface = 13;           // ... and those fitting this one four quadrants per warp
+  int auto_plain = 0;       // RT_SCHED_AUTO takes the plain schedule (autotuner's choice)
   int warps_per_block = 8;  // warp-mode CTA size of the last trace (1..8 warps)
   unsigned long long* counters = nullptr;  // [0]: rate evaluations of the last trace
   double2* bwd_stack = nullptr;  // adjoint: per-CTA (tau_in, tau_out) stacks
