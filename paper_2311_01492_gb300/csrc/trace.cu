@@ -439,9 +439,12 @@ __device__ __forceinline__ void flush_rate_count(const TraceArgs& a, unsigned nr
   if ((threadIdx.x & 31) == 0 && nrate) atomicAdd(a.rate_cells, (unsigned long long)nrate);
 }
 
-// CTA mode: the whole CTA traces one item at a time (large sources).
+// CTA mode: the whole CTA traces one item at a time (large sources).  Nine
+// 128-thread CTAs per SM (56 registers; the shared memory of nine fits) measured
+// faster than eight at 64 or fewer at 72-80 registers: latency, not registers,
+// limits this loop.
 template <int BLOCK, bool COLDENS>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_trace_faces(TraceArgs a) {
+__global__ void __launch_bounds__(BLOCK, 1152 / BLOCK) k_trace_faces(TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
   if (a.skip && *a.skip) return;

@@ -181,6 +181,23 @@ def test_large_radii_wide_layers():
     run_both(w, table("bb"), schedules=("batched",), cd_srcs=(1,), sched=(256, 27, 13))
 
 
+def test_autotuned_auto_schedule():
+    """rt_autotune picks a batched configuration and whether the plain schedule is
+    faster; RT_SCHED_AUTO then runs that choice, with the same rates."""
+    from paper_2311_01492_gb300 import _lib as L
+    w = _random_box(24, 40, 12.0, 3)
+    tab = table("bb")
+    ref = O.raytrace(w["n"], w["cell_cm"], w["nH"], w["xHI"], w["pos"], w["ndot"], w["radius"],
+                     tab, nthreads=8)
+    g = make_gpu(w["n"], w["cell_cm"], w["nH"], w["xHI"], w["pos"], w["ndot"], w["radius"], tab)
+    block, hsmall, hface = g.autotune()
+    assert block in (128, 256) and 0 <= hsmall <= 32 and 0 <= hface <= 20
+    gam = g.raytrace(schedule="auto").cpu().numpy()
+    assert g.stats()["schedule"] in (L.RT_SCHED_PLAIN, L.RT_SCHED_BATCHED)
+    assert_gamma(gam, ref["gamma"])
+    g.close()
+
+
 def test_degenerate_sizes():
     # one-cell box, radius below one cell, zero rate, huge radius clipped by the window
     for n, R, nd in [(1, 5.0, 1e50), (8, 0.5, 1e50), (8, 100.0, 0.0), (2, 3.0, 1e49)]:
