@@ -162,11 +162,12 @@ def oracle_sample(w, target_s, cores):
                    w["radius"][idx], tab, nthreads=cores)
         return sv, time.perf_counter() - t0, len(idx)
 
-    sv, dt, k = run(max(cores * 8, 256))          # calibration
-    rate = sv / dt
-    per_src = sv / k
-    k2 = int(min(nsrc, max(k, target_s * rate / per_src)))
-    sv, dt, k = run(k2)
+    sv, dt, k = run(max(cores * 8, 256))          # calibration (includes start-up costs)
+    for _ in range(3):  # grow the sample until it takes about target_s
+        k2 = int(min(nsrc, max(k, k * target_s / max(dt, 1e-3))))
+        sv, dt, k = run(k2)
+        if dt >= 0.6 * target_s or k >= nsrc:
+            break
     return sv / dt, dt, k, sv
 
 
