@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <map>
 #include <vector>
 
 #include "../../include/asora.h"
@@ -151,6 +152,7 @@ struct Grid {
   int64_t source_voxels = 0;
   std::vector<int> r2_sorted_h;  // per merged source (LPT order), host copy
   size_t src_cap = 0;            // sources the arrays above (and items / 24) can hold
+  std::map<std::pair<int, int>, int64_t> ball_memo;  // traced cells per (R^2 limit, box size)
   // scratch of the source ingest, kept between calls and grown on demand
   struct Ingest {
     size_t cap = 0;  // sources the per-source arrays hold

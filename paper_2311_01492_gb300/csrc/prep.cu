@@ -397,7 +397,7 @@ rt_status ingest_sources(Grid& g, int nsrc, const int32_t* d_pos, const int32_t*
   CK(cudaStreamSynchronize(s));
   {
     g.r2_sorted_h.assign(w.r2pin, w.r2pin + nm);
-    std::map<std::pair<int, int>, int64_t> memo;
+    std::map<std::pair<int, int>, int64_t>& memo = g.ball_memo;  // kept between calls
     int64_t sv = 0, last_cnt = 0;
     std::pair<int, int> last_key(-1, -1);
     for (int p = 0; p < nm; ++p) {  // sources come sorted by r2: runs of equal keys
