@@ -272,6 +272,14 @@ def test_invalid_inputs_are_rejected():
     g.set_sources(dev([[1, 2, 3]], torch.int32), dev([1e50]), dev([3.0]))
     gam = g.raytrace()
     assert torch.count_nonzero(gam).item() > 0
+    for bad in (0.0, -1.0, float("nan"), float("inf"), 1e7):
+        with pytest.raises(api.RtError, match="RT_ERR_INVALID"):
+            g.set_scale_factor(bad)
+    for sched in [(64, 19, 13), (128, -1, 0), (128, 33, 0), (256, 19, 21), (128, 19, -1)]:
+        with pytest.raises(api.RtError, match="RT_ERR_INVALID"):
+            g.set_schedule(*sched)
+    # rejected calls leave the grid as it was
+    assert torch.equal(g.raytrace(), gam)
     g.close()
 
 
