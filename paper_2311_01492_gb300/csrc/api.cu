@@ -873,9 +873,9 @@ rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_
   // (RT_SCHED_AUTO then takes the faster)
   if (st == RT_OK) {
     float tp = 0.f;
+    TRY(cudaMalloc(&gam, g.ncell * sizeof(double)));
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    TRY(cudaMalloc(&gam, g.ncell * sizeof(double)));
     cudaEventRecord(e0, g.stream);
     st = rt_raytrace(h, gam, RT_SCHED_PLAIN);
     cudaEventRecord(e1, g.stream);
