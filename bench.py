@@ -428,7 +428,7 @@ def main():
     traffic = measured_traffic(exact_sv)
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved_tf / peak_tf, "traffic": traffic,
-                "kernel": "k_trace_faces + k_trace_faces_warp (FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "kernel": "k_trace_faces + k_trace_faces_warp + k_trace_faces4_warp (the batched trace; FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz)",
                 "algorithmic_flops_per_launch": flops,
                 "hbm_view": {"achieved_gbs": BYTES_PER_SV * exact_sv / (tr_ms * 1e-3) / 1e9,
                              "peak_gbs": hbm_peak,
