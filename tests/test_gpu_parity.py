@@ -304,6 +304,32 @@ def test_chemistry_step_matches_oracle():
     g.close()
 
 
+def test_chemistry_convergence_count_hand_built_cells():
+    """The unconverged-cell count that stops rt_iterate (Sec. 2.1, Fig. 1), on the
+    hand-built cells the oracle is pinned with (no radiation, collisions or
+    recombination, so <x> = x0 exactly): the same count, exactly."""
+    api = A()
+    tol = 2.0 ** -10
+    x0 = np.full(27, 0.5)
+    xa_in = np.full(27, 0.5)
+    cells = [(0.5, 0.5 - 2.0 ** -12), (0.5, 0.5 - 2.0 ** -10), (0.5, 0.5 - 2.0 ** -11),
+             (0.5, 0.5 + 2.0 ** -11), (0.5, 0.49951146), (0.998046875, 0.998046875 - 2.0 ** -18),
+             (0.001953125, 0.001953125 - 2.0 ** -12), (0.0, 0.0),
+             (1.0 - 2.0 ** -20, 1.0 - 2.0 ** -20 - 2.0 ** -29)]
+    for c, (a, b) in enumerate(cells):
+        x0[c], xa_in[c] = a, b
+    g = api.Grid(3, S.KPC_CM)
+    g.set_density(dev(np.full(27, 1e-3)))
+    xa, xn, cnt = g.chemistry_step(dev(np.zeros(27)), dev(x0), dev(xa_in), S.MYR_S, alpha_H=0.0,
+                                   C_H=0.0, conv_tol=tol)
+    _, _, cnt_o = O.chemistry(np.full(27, 1e-3), x0, xa_in, np.zeros(27), S.MYR_S, alpha_H=0.0,
+                              C_H=0.0, conv_tol=tol)
+    assert cnt_o == 4
+    assert int(cnt.item()) == 4
+    assert np.array_equal(xa.cpu().numpy(), x0) and np.array_equal(xn.cpu().numpy(), x0)
+    g.close()
+
+
 def _oracle_step(n, cell, nH, x, src, ndot, R, tab, dt, iters):
     xa = x.copy()
     for _ in range(iters):

@@ -281,6 +281,34 @@ def test_optically_thin_limit():
         assert g[c, c, c + k] == pytest.approx(local, rel=1e-6)
 
 
+def test_thin_source_cell_conserves_photons():
+    """The source cell in the thin limit (Sec. 3.3 "treated directly", Eq. gammalocal).
+
+    Half a cell of column is crossed, so the photons absorbed in the cell are
+    Ndot (1 - e^(-dtau/2)) -> Ndot dtau/2 for dtau -> 0; per neutral atom of the
+    alpha^3 cell that is Gamma_s = Ndot sigma0 / (2 alpha^2) for grey opacity
+    (h(0) = 1).  The oracle's thin branch must give that value, and its thick
+    branch must tend to it as dtau shrinks towards the switch."""
+    a = CELL32
+    ndot = 3e53
+    want = ndot * O.SIGMA0 / (2.0 * a * a)
+    r, tau, c, dt = _uniform(xhi=1e-12, ndot=ndot)
+    assert 0.5 * dt <= O.TAU_LIM  # the thin branch is the one taken
+    g = r["gamma"].reshape(32, 32, 32)
+    assert g[c, c, c] == pytest.approx(want, rel=1e-13)
+    # photon balance of the same cell: Gamma_s n_HI alpha^3 = Ndot * dtau/2
+    nhi = 1e-3 * 1e-12
+    assert g[c, c, c] * nhi * a ** 3 == pytest.approx(ndot * 0.5 * dt, rel=1e-13)
+    # thick branch just above the switch: Ndot (1 - e^(-dtau/2)) / (n_HI alpha^3)
+    for xhi in (1e-9, 1e-8):
+        r, tau, c, dt = _uniform(xhi=xhi, ndot=ndot)
+        assert 0.5 * dt > O.TAU_LIM
+        g = r["gamma"].reshape(32, 32, 32)
+        thick = ndot * (-math.expm1(-0.5 * dt)) / (1e-3 * xhi * a ** 3)
+        assert g[c, c, c] == pytest.approx(thick, rel=1e-9)
+        assert g[c, c, c] == pytest.approx(want, rel=dt)  # 1 - O(dtau/4) from the thin value
+
+
 # ------------------------------------------------------------ tables (Eq. tables)
 def test_grey_knots_are_exponentials():
     g, h = O.table_knots("grey")
@@ -389,6 +417,42 @@ def test_chemistry_matches_ode_and_limits():
     xa, xn, _ = O.chemistry([1e-3], [0.0], [0.0], [1e-12], 1e6 * dt, C_H=0.0, tol=1e-14, maxit=500)
     ne = 1e-3 * xa[0]
     assert xn[0] == pytest.approx(1e-12 / (1e-12 + ne * al), rel=1e-9)
+
+
+def test_convergence_count_follows_the_neutral_fraction_rule():
+    """Global convergence test of the iteration (Sec. 2.1, Fig. 1): a cell is
+    unconverged when its neutral fraction 1-<x> moved by more than conv_tol
+    relative to the new neutral fraction.  With no radiation, no collisions and
+    no recombination (Gamma = C_H = alpha_H = 0) the step keeps <x> = x0, so the
+    move is set by the <x> the preceding trace used (xavg_in).  The expected
+    verdicts are written out per cell, not recomputed with the oracle's formula:
+    they fail a count taken on the old neutral fraction, on x_HII instead of
+    x_HI, with >= instead of >, or with the inequality reversed."""
+    tol = 2.0 ** -10
+    cells = [  # (x0, xavg_in, unconverged?)
+        (0.5, 0.5, False),                          # no move
+        (0.5, 0.5 - 2.0 ** -12, False),             # 2^-12 / 0.5 = tol / 2
+        (0.5, 0.5 - 2.0 ** -10, True),              # 2^-10 / 0.5 = 2 tol
+        (0.5, 0.5 - 2.0 ** -11, False),             # exactly tol * x_HI,new: not above
+        (0.5, 0.5 + 2.0 ** -11, False),             # the same move downwards
+        (0.5, 0.49951146, True),                    # tol < 1.0005 tol on x_HI,new; 0.9995 tol on x_HI,old
+        (0.998046875, 0.998046875 - 2.0 ** -18, True),   # x_HI 2^-9: move 2^-18 = 2 tol x_HI
+        (0.001953125, 0.001953125 - 2.0 ** -12, False),  # x_HI ~ 1: move tol/4 of it (x_HII moves 1/8)
+        (0.0, 0.0, False),
+        (1.0 - 2.0 ** -20, 1.0 - 2.0 ** -20 - 2.0 ** -29, True),  # 2^-9 = 2 tol, near full ionisation
+    ]
+    x0 = np.array([c[0] for c in cells])
+    xa_in = np.array([c[1] for c in cells])
+    want = [c[2] for c in cells]
+    zero = np.zeros(len(cells))
+    nH = np.full(len(cells), 1e-3)
+    for k in range(len(cells)):  # one cell at a time: the verdict of each
+        _, xn, cnt = O.chemistry(nH[k:k + 1], x0[k:k + 1], xa_in[k:k + 1], zero[k:k + 1], S.MYR_S,
+                                 alpha_H=0.0, C_H=0.0, conv_tol=tol)
+        assert xn[0] == x0[k]
+        assert cnt == int(want[k]), "cell %d" % k
+    _, _, cnt = O.chemistry(nH, x0, xa_in, zero, S.MYR_S, alpha_H=0.0, C_H=0.0, conv_tol=tol)
+    assert cnt == 4
 
 
 # ------------------------------------------------------------ Stromgren (Sec. 4.1.1)
