@@ -56,8 +56,8 @@ def parse():
     ap.add_argument("--hsmall", type=int, default=19,
                     help="with --no-autotune: largest layer half-width traced by single warps")
     ap.add_argument("--hface", type=int, default=13,
-                    help="with --no-autotune: largest layer half-width traced by packed warps "
-                         "(four quadrants of a face per warp; 0 = off)")
+                    help="with --no-autotune: largest layer half-width whose faces one warp "
+                         "traces whole (0 = off)")
     ap.add_argument("--adjoint-src", type=int, default=100_000,
                     help="sources of the gradient-throughput measurement (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -428,7 +428,7 @@ def main():
     traffic = measured_traffic(exact_sv)
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved_tf / peak_tf, "traffic": traffic,
-                "kernel": "k_trace_faces + k_trace_faces_warp + k_trace_faces4_warp (the batched trace; FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "kernel": "k_trace_faces + k_trace_faces_warp + k_trace_faces_whole_warp (the batched trace; FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz)",
                 "algorithmic_flops_per_launch": flops,
                 "hbm_view": {"achieved_gbs": BYTES_PER_SV * exact_sv / (tr_ms * 1e-3) / 1e9,
                              "peak_gbs": hbm_peak,
@@ -462,7 +462,7 @@ def main():
                        "nsrc": len(w["ndot"]), "radius_cells": "5-50 (R=5(Ndot/1e50)^0.2)",
                        "schedule": "batched (persistent, 24 face-quadrant items/source, LPT "
                                    "queue; CTA %d threads, warp mode for layer half-width "
-                                   "<= %d, four quadrants per warp for <= %d)" % tuned,
+                                   "<= %d, whole faces per warp for <= %d)" % tuned,
                        "step": "ingest + dtau + trace + chemistry",
                        "l2": "512 MB write between steps; fields 3 x 125 MB > L2",
                        "per_rank": "independent box per rank (weak scaling)"},

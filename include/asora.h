@@ -199,17 +199,17 @@ typedef struct {
   int64_t row_table_bytes;  /* precomputed row tables of the ingested radii (0: none) */
 } rt_stats;
 
-/* Schedule of RT_SCHED_BATCHED: items of sources whose largest layer half-width
- * exceeds hsmall are traced by CTAs of block_big threads (128 or 256), the
- * others by single warps (hsmall 0..32; 0 = CTAs only); of those, sources whose
- * largest layer half-width is at most hface (0..20; 0 = off) are traced by warps
- * that take the four quadrants of a face together.  Defaults 128, 19, 13;
- * results do not depend on the choice. */
+/* Schedule of RT_SCHED_BATCHED: (face, quadrant) items of sources whose largest
+ * layer half-width exceeds hsmall are traced by CTAs of block_big threads (128 or
+ * 256), the others by single warps (hsmall 0..32; 0 = CTAs only); of those,
+ * sources whose largest layer half-width is at most hface (0..20; 0 = off) have
+ * each face traced whole by one warp (every cell of a face once, no cell shared
+ * between quadrants).  Defaults 128, 19, 13; results do not depend on the choice. */
 rt_status rt_set_schedule(rt_grid_t g, int block_big, int hsmall, int hface);
 
 /* Autotuner of RT_SCHED_BATCHED: times rt_raytrace on the registered fields and
  * sources for block_big in {128, 256} x hsmall in {0, 11, 15, 19, 22, 24, 27, 30}
- * (packed warps off), then hface in {9, 11, 13, 15, 17, 19} at the fastest pair; keeps
+ * (whole-face warps off), then hface in {9, 11, 13, 15, 17, 19} at the fastest pair; keeps
  * the fastest and returns it in *h_block, *h_hsmall, *h_hface (any may be NULL).
  * Finally times the plain (block-per-source) schedule once: RT_SCHED_AUTO takes
  * whichever of the two is faster.  With a cache file (may be NULL), a line

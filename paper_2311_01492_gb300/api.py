@@ -202,7 +202,7 @@ class Grid:
                 "rt_set_adjoint_mode")
 
     def set_schedule(self, block_big=128, hsmall=19, hface=13):
-        """Batched schedule: CTA size, warp-mode threshold, packed-warp threshold."""
+        """Batched schedule: CTA size, warp-mode threshold, whole-face-warp threshold."""
         L.check(self._lib.rt_set_schedule(self._h, int(block_big), int(hsmall), int(hface)),
                 "rt_set_schedule")
 

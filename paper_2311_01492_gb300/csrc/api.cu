@@ -109,6 +109,8 @@ static TraceArgs base_args(Grid& g) {
   a.rtab_hcap = g.rtab_hcap;
   a.rtab_slot = g.rtab_slot;
   a.rtab_max_r2 = g.rtab_max_r2;
+  a.itab = g.itab;
+  a.itab_off = g.itab_off;
   a.neg_zero = -0.0;
   a.geo_mmax = g.geo_mmax;
   a.tab.g = g.gtab;
@@ -189,10 +191,10 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
       return fail(RT_ERR_INVALID, "rt_raytrace: the batched schedule needs boxes of at most "
                                   "1290^3 cells (32-bit offsets); use RT_SCHED_PLAIN");
     // Batched: items of large sources are traced by whole CTAs, items whose
-    // layers fit g.hsmall by single warps, and items whose layers fit g.hface by
-    // single warps that take the four quadrants of a face together.  Items come
+    // layers fit g.hsmall by single warps, and the faces of sources whose layers
+    // fit g.hface by single warps that trace a face whole.  Items come
     // in LPT order (24 per source, r2 non-increasing), so each mode gets a
-    // contiguous range of sources: [0, pw) CTAs, [pw, p4) warps, [p4, ns) packed.
+    // contiguous range of sources: [0, pw) CTAs, [pw, p4) warps, [p4, ns) whole faces.
     const int* r2s = single_r2 >= 0 ? &single_r2 : g.r2_sorted_h.data();
     const int ns = n_items / 24;
     auto first_fitting = [&](int hlim) {  // first source whose layers fit hlim (ns: none)
@@ -262,7 +264,7 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
       rt_status ws = warp_launch(32, face_hcap(r2s[pw], g.nmax), 24 * pw, 24 * p4, g.queue + 1);
       if (ws != RT_OK) return ws;
     }
-    if (ns > p4) {  // packed: face items it -> items[4 it]
+    if (ns > p4) {  // whole faces: face items it -> items[4 it]
       rt_status ws = warp_launch(4, face_hcap(r2s[p4], g.nmax), 6 * p4, 6 * ns, g.queue + 2);
       if (ws != RT_OK) return ws;
     }
@@ -530,7 +532,7 @@ rt_status rt_get_stats(rt_grid_t h, rt_stats* out) {
   TRY(cudaMemcpy(&rc, g.counters, sizeof(rc), cudaMemcpyDeviceToHost));
   g.stats.rate_cells = (int64_t)rc;
   g.stats.kernel_launches = g_launches.load();
-  g.stats.row_table_bytes = g.rtab ? g.rtab_bytes : 0;
+  g.stats.row_table_bytes = g.rtab ? g.rtab_bytes + g.itab_bytes : 0;
   *out = g.stats;
   int herr = 0;
   TRY(cudaMemcpy(&herr, g.err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -831,8 +833,8 @@ rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_
     }
     return st == RT_OK;
   };
-  // stage 1: CTA size x warp-mode threshold (packed warps off); stage 2: the
-  // packed-warp threshold at the chosen pair
+  // stage 1: CTA size x warp-mode threshold (whole-face warps off); stage 2: the
+  // whole-face threshold at the chosen pair
   const int blocks[] = {128, 256};
   const int hss[] = {0, 11, 15, 19, 22, 24, 27, 30};
   const int hfs[] = {9, 11, 13, 15, 17, 19};

@@ -104,6 +104,10 @@ struct TraceArgs {
   const int* rtab_hcap;   // largest layer half-width of each R^2 limit
   const int* rtab_slot;   // R^2 limit -> slot, for 0..rtab_max_r2
   int rtab_max_r2;        // -1: no tables
+  // Interior row tables of the same (R^2 limit, m) layers, for faces traced
+  // whole (see k_interior_tables): blob of layer m at itab + itab_off[same index].
+  const unsigned char* itab;
+  const int* itab_off;
 };
 
 enum ErrBits { ERR_LAYER_CAP = 1, ERR_GEO = 2, ERR_INPUT = 4, ERR_CUBE = 8 };
@@ -180,6 +184,9 @@ struct Grid {
   int rtab_max_r2 = -1;
   int rtab_mcap = 0;
   int64_t rtab_bytes = 0;
+  unsigned char* itab = nullptr;  // interior row tables (faces traced whole)
+  int* itab_off = nullptr;
+  int64_t itab_bytes = 0;
   std::vector<int> rtab_r2s;  // the R^2 limits the tables were built for (descending)
 
   // geometry
@@ -200,7 +207,7 @@ struct Grid {
   int* flags = nullptr;
   int block_big = 128;      // threads per CTA for large-source items
   int hsmall = 19;          // items whose layers fit this half-width run one per warp
-  int hface = 13;           // ... and those fitting this one four quadrants per warp
+  int hface = 13;           // ... and those fitting this one whole faces per warp
   int auto_plain = 0;       // RT_SCHED_AUTO takes the plain schedule (autotuner's choice)
   int warps_per_block = 8;  // warp-mode CTA size of the last trace (1..8 warps)
   unsigned long long* counters = nullptr;  // [0]: rate evaluations of the last trace

@@ -87,12 +87,18 @@ __host__ __device__ inline size_t group_smem_bytes(int h, bool warp) {
   return layer_bytes(h, warp) + 2 * (size_t)row_slot_bytes(h);
 }
 
-// Shared memory of one warp tracing the four quadrants of a face together:
-// four in-place layers of (h+1)^2 doubles, then two row-table slots (shared by
-// the quadrants).  Also holds the single-quadrant layout of group_smem_bytes.
-__host__ __device__ inline size_t face4_smem_bytes(int h) {
-  const size_t cap = (size_t)(h + 1) * (h + 1);
-  return ((4 * cap * sizeof(double) + 15) & ~(size_t)15) + 2 * (size_t)row_slot_bytes(h);
+// Shared memory of one warp tracing a whole face: the face layer, (2h+1)^2
+// doubles updated in place (slot of transverse offset (t1, t2) at
+// (t1+h)(2h+1) + t2+h), then two slots for the interior row tables (the current
+// layer's and the next's).  At least the single-quadrant warp layout of
+// group_smem_bytes, which faces clipped by the window use instead.
+__host__ __device__ inline size_t face_buf_bytes(int h) {
+  return ((size_t)(2 * h + 1) * (2 * h + 1) * sizeof(double) + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t whole_smem_bytes(int h) {
+  const size_t w = face_buf_bytes(h) + 2 * (size_t)row_slot_bytes(h);
+  const size_t q = group_smem_bytes(h, true);
+  return w > q ? w : q;
 }
 
 // Asynchronous copy of a precomputed row-table blob (16-byte aligned, size a

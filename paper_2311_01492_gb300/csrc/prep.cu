@@ -472,10 +472,56 @@ __global__ void k_row_tables(const int* __restrict__ ent_r2, const int* __restri
     rtab[off[e] + b] = 0;
 }
 
+// Interior row tables of the same layers, for faces traced whole by one warp:
+// layer m of a face holds the transverse offsets |t1|, |t2| <= H with
+// t1^2 + t2^2 <= r2 - m^2; its interior positions (1 <= a1, a2 <= m-1) form rows
+// a1 = 1..LA, LA = min(H, m-1), row a1 holding a2 = 1..min(H, isqrt(r2 - m^2 -
+// a1^2), m-1).  Blob: rowpre[0..LA] (ints: first flat index of row r = a1-1,
+// then the number of positions) and rowof[0..total) (bytes: row of every flat
+// index).  The axes and the rim of the layer are enumerated arithmetically.
+__device__ __forceinline__ int isqrt_dev(int x) {
+  int w = (int)sqrtf((float)x);
+  while (w * w > x) --w;
+  while ((w + 1) * (w + 1) <= x) ++w;
+  return w;
+}
+
+__global__ void k_interior_tables(const int* __restrict__ ent_r2, const int* __restrict__ ent_m,
+                                  const int* __restrict__ off, unsigned char* __restrict__ itab,
+                                  int nent) {
+  const int e = blockIdx.x;
+  if (e >= nent) return;
+  const int m = ent_m[e];
+  const int rem = ent_r2[e] - m * m;
+  const int H = min(isqrt_dev(rem), m);
+  const int LA = min(H, m - 1);
+  int* rowpre = reinterpret_cast<int*>(itab + off[e]);
+  unsigned char* rowof = reinterpret_cast<unsigned char*>(rowpre + LA + 1);
+  __shared__ int pre[256 + 1];
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int r = 0; r < LA; ++r) {
+      pre[r] = run;
+      const int a1 = r + 1;
+      run += max(0, min(min(H, isqrt_dev(rem - a1 * a1)), m - 1));
+    }
+    pre[LA] = run;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r <= LA; r += blockDim.x) rowpre[r] = pre[r];
+  for (int r = 0; r < LA; ++r)
+    for (int c = pre[r] + threadIdx.x; c < pre[r + 1]; c += blockDim.x) rowof[c] = (unsigned char)r;
+  const int used = 4 * (LA + 1) + pre[LA];
+  for (int b = used + threadIdx.x; b < off[e + 1] - off[e]; b += blockDim.x)
+    itab[off[e] + b] = 0;
+}
+
 void free_row_tables(Grid& g) {
   cudaFree(g.rtab); cudaFree(g.rtab_off); cudaFree(g.rtab_first); cudaFree(g.rtab_hcap);
-  cudaFree(g.rtab_slot);
+  cudaFree(g.rtab_slot); cudaFree(g.itab); cudaFree(g.itab_off);
   g.rtab = nullptr; g.rtab_off = g.rtab_first = g.rtab_hcap = g.rtab_slot = nullptr;
+  g.itab = nullptr; g.itab_off = nullptr;
+  g.itab_bytes = 0;
   g.rtab_max_r2 = -1;
   g.rtab_bytes = 0;
   g.rtab_r2s.clear();
@@ -497,8 +543,8 @@ rt_status ensure_row_tables(Grid& g) {
     g.rtab_mcap = mcap;
     return RT_OK;
   }
-  std::vector<int> ent_r2, ent_m, off, first(r2s.size()), hcap(r2s.size());
-  int64_t cur = 0;
+  std::vector<int> ent_r2, ent_m, off, ioff, first(r2s.size()), hcap(r2s.size());
+  int64_t cur = 0, icur = 0;
   for (size_t i = 0; i < r2s.size(); ++i) {
     const int v = r2s[i];
     const int L = std::min(isqrt_host(v), mcap);
@@ -509,11 +555,17 @@ rt_status ensure_row_tables(Grid& g) {
       const int H = std::min(m, isqrt_host(rem));
       int64_t total = 0;
       for (int r = 0; r <= H; ++r) total += std::min(H, isqrt_host(rem - (int64_t)r * r)) + 1;
+      const int LA = std::min(H, m - 1);
+      int64_t itotal = 0;
+      for (int a1 = 1; a1 <= LA; ++a1)
+        itotal += std::max(0, std::min(std::min(H, isqrt_host(rem - (int64_t)a1 * a1)), m - 1));
       hc = std::max(hc, H);
       ent_r2.push_back(v);
       ent_m.push_back(m);
       off.push_back((int)cur);
+      ioff.push_back((int)icur);
       cur += (4 * (int64_t)(H + 2) + total + 15) & ~(int64_t)15;
+      icur += (4 * (int64_t)(LA + 1) + itotal + 15) & ~(int64_t)15;
       if (cur > (int64_t)1 << 30 || H > 254) {  // keep offsets in int, rows in bytes
         g.rtab_r2s = r2s;
         g.rtab_mcap = mcap;
@@ -523,6 +575,7 @@ rt_status ensure_row_tables(Grid& g) {
     hcap[i] = hc;
   }
   off.push_back((int)cur);
+  ioff.push_back((int)icur);
   const int nent = (int)ent_m.size();
   const int maxv = r2s.front();
   std::vector<int> slot(maxv + 1, -1);
@@ -543,6 +596,9 @@ rt_status ensure_row_tables(Grid& g) {
   CK(cudaMalloc(&g.rtab_first, first.size() * sizeof(int)));
   CK(cudaMalloc(&g.rtab_hcap, hcap.size() * sizeof(int)));
   CK(cudaMalloc(&g.rtab_slot, slot.size() * sizeof(int)));
+  CK(cudaMalloc(&g.itab, std::max<int64_t>(icur, 16)));
+  CK(cudaMalloc(&g.itab_off, ioff.size() * sizeof(int)));
+  CK(cudaMemcpyAsync(g.itab_off, ioff.data(), ioff.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaMalloc(&d_r2, std::max(nent, 1) * sizeof(int)));
   CK(cudaMalloc(&d_m, std::max(nent, 1) * sizeof(int)));
   CK(cudaMemcpyAsync(g.rtab_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -556,12 +612,16 @@ rt_status ensure_row_tables(Grid& g) {
     k_row_tables<<<nent, 64, 0, s>>>(d_r2, d_m, g.rtab_off, g.rtab, nent);
     count_launch();
     CK(cudaGetLastError());
+    k_interior_tables<<<nent, 64, 0, s>>>(d_r2, d_m, g.itab_off, g.itab, nent);
+    count_launch();
+    CK(cudaGetLastError());
   }
   CK(cudaStreamSynchronize(s));  // host vectors go out of scope
   cudaFree(d_r2);
   cudaFree(d_m);
   g.rtab_max_r2 = maxv;
   g.rtab_bytes = cur;
+  g.itab_bytes = icur;
   g.rtab_r2s = r2s;
   g.rtab_mcap = mcap;
   return RT_OK;

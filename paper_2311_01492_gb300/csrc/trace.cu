@@ -30,7 +30,9 @@
 // persistent groups: CTAs (k_trace_faces) for items with wide layers, single
 // warps (k_trace_faces_warp) for the others.  A quadrant layer lives in shared
 // memory ((H+1)^2 doubles; two buffers per CTA, one updated in place per
-// warp), so a cell reads only the previous layer of its own item.
+// warp), so a cell reads only the previous layer of its own item.  The faces of
+// small sources are traced whole by one warp (k_trace_faces_whole_warp): a
+// (2h+1)^2 layer updated in place, every cell of a face computed once.
 #include <algorithm>
 #include <cmath>
 
@@ -40,9 +42,9 @@
 namespace asora {
 
 // ----------------------------------------------------------- face kernels
-// block codes: 128/256 CTA mode, 32 warp mode, 4 packed warp mode
+// block codes: 128/256 CTA mode, 32 warp mode, 4 whole-face warp mode
 size_t faces_smem_bytes(int hcap, int block) {
-  return block == 4 ? face4_smem_bytes(hcap) : group_smem_bytes(hcap, block == 32);
+  return block == 4 ? whole_smem_bytes(hcap) : group_smem_bytes(hcap, block == 32);
 }
 
 // Trace one (source, face, quadrant) item with a group of GS threads (gt =
@@ -256,20 +258,8 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
   }
 }
 
-// Packed mode: a group of GS threads (one warp, or a CTA) traces the four
-// quadrants of a face together.  Thread u of a round takes cell t = u >> 2 of
-// quadrant k = u & 3, so the four threads of a cell position share its row-table
-// and geometry loads, and a round holds four times as many cells as with one
-// quadrant.  Each quadrant keeps its own layer buffer, updated in place: the
-// cells are taken in descending order of u, GS at a time, every thread of the
-// group reads its interpolants before any thread writes (a barrier per round in
-// a CTA, a warp sync in a warp), and a cell reads only slots whose flat index is
-// not above its own -- later rounds cover smaller t, so no slot is rewritten
-// before it is read (a round starts at u = 3 mod 4, so every thread keeps one
-// quadrant).  Items whose window clips a layer (no precomputed tables) are traced
-// quadrant by quadrant instead.
-// The four quadrants of a face one after another (clipped windows), kept out of
-// line so that it does not weigh on the registers of the packed loop.
+// The four quadrants of a clipped face one after another, kept out of line so
+// that it does not weigh on the registers of the whole-face loop.
 template <int GS, bool COLDENS>
 __device__ __noinline__ void trace_face_by_quadrants(const TraceArgs& a, const int item,
                                                      const int gt, unsigned char* sm, const int h,
@@ -280,27 +270,83 @@ __device__ __noinline__ void trace_face_by_quadrants(const TraceArgs& a, const i
   }
 }
 
+// Cells of layer m of an unclipped face, as one list in the order the in-place
+// update needs (j ascending):
+//   E row: |t1| = m    (2 + 4 LE entries: (+-m, 0), then (+-m, +-a2), a2 = 1..LE)
+//   E col: |t2| = m, |t1| < m   (2 + 4 min(LE, m-1) entries)
+//   I:     1 <= |t1|, |t2| <= m-1, the four sign images of each interior position
+//          of the quadrant, positions in descending row-table order
+//   A:     the axes, levels a = LA..1 descending, images (0,+a) (0,-a) (+a,0) (-a,0),
+//          then (0, 0)
+// with LE = min(m, isqrt(rem - m^2)) (E exists only if the layer reaches |t| = m)
+// and LA = min(H, m-1).  cls: which weights can be non-zero.
+enum { CLS_EROW = 0, CLS_ECOL = 1, CLS_I = 2, CLS_AT1 = 3, CLS_AT2 = 4 };
+
+__device__ __forceinline__ void face_cell(const int j, const int m, const int nEr, const int nE,
+                                          const int nI, const int LA,
+                                          const int* __restrict__ rowpre,
+                                          const unsigned char* __restrict__ rowof, int& t1,
+                                          int& t2, int& cls) {
+  if (j < nEr) {
+    cls = CLS_EROW;
+    const int u = j - 2, a2 = 1 + (u >> 2), k = u & 3;
+    t1 = (j < 2 ? j : k) & 1 ? -m : m;
+    t2 = j < 2 ? 0 : ((k & 2) ? -a2 : a2);
+  } else if (j < nE) {
+    cls = CLS_ECOL;
+    const int v = j - nEr, u = v - 2, a1 = 1 + (u >> 2), k = u & 3;
+    t1 = v < 2 ? 0 : ((k & 1) ? -a1 : a1);
+    t2 = (v < 2 ? v : (k >> 1)) & 1 ? -m : m;
+  } else if (j < nE + 4 * nI) {
+    cls = CLS_I;
+    const int u = j - nE, p = nI - 1 - (u >> 2), k = u & 3;
+    const int r = rowof[p];
+    const int a1 = r + 1, a2 = p - rowpre[r] + 1;
+    t1 = (k & 1) ? -a1 : a1;
+    t2 = (k & 2) ? -a2 : a2;
+  } else {
+    const int u = j - nE - 4 * nI, lvl = LA - (u >> 2), k = u & 3;
+    const bool on_t2 = k < 2 && u < 4 * LA;  // t1 = 0 and t2 != 0
+    cls = on_t2 ? CLS_AT1 : CLS_AT2;
+    const int sgn = (k & 1) ? -lvl : lvl;
+    t1 = on_t2 || u >= 4 * LA ? 0 : sgn;
+    t2 = on_t2 ? sgn : 0;
+  }
+}
+
+// Trace one face of one source (item = its quadrant-0 item) with a group of GS
+// threads: a CTA (GS > 32) or one warp (GS == 32).  The face layer lives in one
+// buffer, updated in place; the cells of layer m are taken from the list of
+// face_cell, GS at a time, and each round reads all its interpolants before any
+// thread writes (a barrier, or a warp sync).  A cell's non-zero-weight
+// interpolants are cells of layer m-1 that come at or after it in the list
+// (I positions in descending row-table order read positions not above their
+// own; the axes read only the axes, which come last, inward; the E cells read
+// |t| = m-1), so no slot is rewritten before it is read.  Weights of zero may
+// read any slot: every slot holds a finite value (zeroed at kernel start).
+// Rounds whose cells all lie on an axis or on the face's rim have two non-zero
+// weights per cell and take the two-term form, which rounds exactly like the
+// full chain (the zero terms add exactly +0).  Faces whose layers the window
+// clips are traced quadrant by quadrant (trace_face_item) instead.
 template <int GS, bool COLDENS>
-__device__ __forceinline__ void trace_face4(const TraceArgs& a, const int item, const int gt,
-                                            unsigned char* __restrict__ sm, const int h,
-                                            unsigned& nrate) {
-  const int lane = gt & 31;
+__device__ __forceinline__ void trace_face_whole(const TraceArgs& a, const int item, const int gt,
+                                                 unsigned char* __restrict__ sm, const int h,
+                                                 unsigned& nrate) {
   const int s = item >> 5, f = (item >> 2) & 7;
   const SrcDev S = a.src[s];
   const BoxDev B = a.boxes[S.box];
   const int R2 = a.r2lim[s];
+  // interior row tables of this limit (blob of layer m at itab + toff[m]), used
+  // when no window clips the face's layers
   const int* toff = nullptr;
-  if (R2 <= a.rtab_max_r2) {
+  if (R2 <= a.rtab_max_r2 && a.itab) {
     const int sl = a.rtab_slot[R2];
-    if (sl >= 0 && a.rtab_hcap[sl] <= min(B.whi, -B.wlo)) toff = a.rtab_off + a.rtab_first[sl] - 1;
+    if (sl >= 0 && a.rtab_hcap[sl] <= min(B.whi, -B.wlo)) toff = a.itab_off + a.rtab_first[sl] - 1;
   }
   if (!toff) {
-    trace_face_by_quadrants<GS, COLDENS>(a, item, gt, sm, h, nrate);
+    trace_face_by_quadrants<GS, COLDENS>(a, item & ~3, gt, sm, h, nrate);
     return;
   }
-  const int cap = (h + 1) * (h + 1), W = h + 1;
-  const int TS = row_slot_bytes(h);
-  unsigned char* tab2 = sm + ((4 * (size_t)cap * sizeof(double) + 15) & ~(size_t)15);  // [2][TS]
   const int N = B.n;
   const double nd = a.ndot[s];
   const int d = f >> 1;
@@ -335,13 +381,15 @@ __device__ __forceinline__ void trace_face4(const TraceArgs& a, const int item, 
   const int md = d == 1 ? N : NN;
   const double* __restrict__ fld = (d == 2 ? a.dtauT : a.dtau) + B.off;
 
-  const int k = 3 - (gt & 3);  // this thread's quadrant for every round
-  const int q1 = (k & 1) ? -1 : 1, q2 = (k & 2) ? -1 : 1;
-  double* qb = reinterpret_cast<double*>(sm) + k * cap;
-  int Hp = 0;
+  const int W = 2 * h + 1;
+  double* ctr = reinterpret_cast<double*>(sm) + h * W + h;  // slot of (t1, t2): ctr[t1 W + t2]
+  const int TS = row_slot_bytes(h);
+  unsigned char* tab2 = sm + face_buf_bytes(h);  // [2][TS], 16-byte aligned
   const bool exit_ok = !COLDENS && a.early_exit;
+  const double half_dts = 0.5 * dts;
+  // interior tables of layer 1 (slot 1); layer m+1's (slot (m+1)&1) during layer m
   if (Lmax >= 1 && min(1, isqrt_i(R2 - 1)) <= h) {
-    stage_rows<GS>(a.rtab + toff[1], toff[2] - toff[1], tab2 + TS, gt);
+    stage_rows<GS>(a.itab + toff[1], toff[2] - toff[1], tab2 + TS, gt);
     cp_async_wait_all();
   }
   group_sync<GS>();
@@ -352,56 +400,73 @@ __device__ __forceinline__ void trace_face4(const TraceArgs& a, const int item, 
       if (gt == 0) atomicOr(a.err, H > h ? ERR_LAYER_CAP : ERR_GEO);
       break;
     }
-    const int nrows = H + 1;
-    const int* rowpre = reinterpret_cast<const int*>(tab2 + (m & 1) * TS);
-    const unsigned char* rowof = reinterpret_cast<const unsigned char*>(rowpre + nrows + 1);
-    const int total = rowpre[nrows];
     int Hn = 0;
     if (m < Lmax) {
       Hn = min(m + 1, isqrt_i(R2 - (m + 1) * (m + 1)));
       if (Hn <= h)
-        stage_rows<GS>(a.rtab + toff[m + 1], toff[m + 2] - toff[m + 1], tab2 + ((m + 1) & 1) * TS,
+        stage_rows<GS>(a.itab + toff[m + 1], toff[m + 2] - toff[m + 1], tab2 + ((m + 1) & 1) * TS,
                        gt);
     }
+    const int LA = min(H, m - 1);
+    const int* rowpre = reinterpret_cast<const int*>(tab2 + (m & 1) * TS);
+    const unsigned char* rowof = reinterpret_cast<const unsigned char*>(rowpre + LA + 1);
+    const int nI = rowpre[LA];
+    int nEr = 0, nE = 0;
+    if (H == m) {
+      const int LE = min(m, isqrt_i(rem - m * m));
+      nEr = 2 + 4 * LE;
+      nE = nEr + 2 + 4 * min(LE, m - 1);
+    }
+    const int total = nE + 4 * nI + 4 * LA + 1;
     const int lc = wrapc(cd + sg * m, N);
     const int lay = lc * md;
     const GeoRow* __restrict__ grow = a.georow + georow_index(m, 0, 0);
     const int gbase = (int)geo_index(m, 0, 0);
-    bool opaque = true;
-    for (int t0 = 4 * total - 1; t0 >= 0; t0 -= GS) {
-      const int u = t0 - gt;  // u = 4 t + k; threads below 0 recompute cell 0, write nothing
-      const int t = max(u, 0) >> 2;
-      const int a1 = rowof[t];
-      const int a2 = t - rowpre[a1];
-      const int x1 = wrapc(c1 + q1 * a1, N), x2 = wrapc(c2 + q2 * a2, N);
+    bool opaque = true;  // every cell of this thread has tau_out >= the exit bound
+    for (int j0 = 0; j0 < total; j0 += GS) {
+      const int j = j0 + gt;  // threads past the end recompute the last cell, write nothing
+      int t1, t2, cls;
+      face_cell(min(j, total - 1), m, nEr, nE, nI, LA, rowpre, rowof, t1, t2, cls);
+      const int a1 = abs(t1), a2 = abs(t2);
+      const int x1 = wrapc(c1 + t1, N), x2 = wrapc(c2 + t2, N);
       const int gidx = lay + x1 * m1 + x2;
       const double dtp = __ldg(&fld[gidx]);
       const GeoRow* gr = grow + a1 * (m + 1) + a2;
       const double2 wv0 = __ldg(reinterpret_cast<const double2*>(gr));      // w1, w2
       const double2 wv1 = __ldg(reinterpret_cast<const double2*>(gr) + 1);  // w3, w4
       const double ds = __ldg(&gr->ds);
+      const int o1 = t1 * W + t2;              // slots of (t1, t2), (t1-s1, t2),
+      const int o2 = o1 - sgn_i(t1) * W;       // (t1, t2-s2), (t1-s1, t2-s2)
+      const int o3 = o1 - sgn_i(t2);
+      const int o4 = o2 - sgn_i(t2);
       double tin;
       if (m == 1) {
-        tin = (0.5 * dts) * ds;
+        tin = half_dts * ds;
+      } else if (__all_sync(0xffffffffu, cls != CLS_I)) {
+        // rim row (w1 = w3 = 0), rim column (w1 = w2 = 0), axis t1 = 0 (w2 = w4 = 0),
+        // axis t2 = 0 (w3 = w4 = 0)
+        const bool er = cls == CLS_EROW, ec = cls == CLS_ECOL, rim = er || ec;
+        const double wA = er ? wv0.y : (ec ? wv1.x : wv0.x);
+        const int oA = er ? o2 : (ec ? o3 : o1);
+        const double wB = rim ? wv1.y : (cls == CLS_AT1 ? wv1.x : wv0.y);
+        const int oB = rim ? o4 : (cls == CLS_AT1 ? o3 : o2);
+        tin = fma(wB, ctr[oB], fma(wA, ctr[oA], a.neg_zero));
       } else {
-        const double w1 = wv0.x, w2 = wv0.y, w3 = wv1.x, w4 = wv1.y;
-        const int b1 = min(a1, Hp), b2 = min(a1 - (a1 > 0), Hp);
-        const int e1 = min(a2, Hp), e2 = min(a2 - (a2 > 0), Hp);
-        const double v1 = qb[b1 * W + e1];
-        const double v2 = qb[b2 * W + e1];
-        const double v3 = qb[b1 * W + e2];
-        const double v4 = qb[b2 * W + e2];
-        tin = fma(w4, v4, fma(w3, v3, fma(w2, v2, fma(w1, v1, a.neg_zero))));
+        // w1*c1 as fma(w1, c1, -0.0): the same value for every input (the sum of the
+        // exact product and -0 rounds like the product alone, and +0 + -0 = +0), on
+        // GB300 issued as a DFMA, which retires at least as fast as a DMUL
+        tin = fma(wv1.y, ctr[o4], fma(wv1.x, ctr[o3], fma(wv0.y, ctr[o2],
+                                                           fma(wv0.x, ctr[o1], a.neg_zero))));
       }
       const double tout = fma(dtp, ds, tin);
       group_sync<GS>();  // every thread has read layer m-1 before any thread writes
-      if (u < 0) continue;
-      qb[a1 * W + a2] = tout;
+      if (j >= total) continue;
+      ctr[o1] = tout;
       opaque = opaque && bits_of(tout) >= a.exit_bits;
-      const bool own = ((d == 2) || (d == 1 ? a2 < m : (a1 < m && a2 < m))) &&
-                       (a1 > 0 || q1 > 0) && (a2 > 0 || q2 > 0);
+      const bool own = (d == 2) || (d == 1 ? a2 < m : (a1 < m && a2 < m));
       if (!own) continue;
       if (COLDENS || bits_of(tin) < a.tab.tau_max_bits) {
+        // C-order index of the cell (the z faces gathered from the rotated copy)
         const int64_t cell = B.off + (d == 2 ? (x1 * N + x2) * N + lc : gidx);
         if (COLDENS) {
           a.coldens[cell] = tout / a.sigma0;
@@ -418,6 +483,7 @@ __device__ __forceinline__ void trace_face4(const TraceArgs& a, const int item, 
     }
     if (m < Lmax && Hn <= h) cp_async_wait_all();
     if (exit_ok) {
+      // exact early exit, as in trace_face_item
       bool all_opaque;
       if (GS == 32) {
         __syncwarp();
@@ -429,7 +495,6 @@ __device__ __forceinline__ void trace_face4(const TraceArgs& a, const int item, 
     } else {
       group_sync<GS>();
     }
-    Hp = H;
   }
 }
 
@@ -489,16 +554,19 @@ __global__ void __launch_bounds__(256, 4) k_trace_faces_warp(TraceArgs a) {
   flush_rate_count(a, nrate);
 }
 
-// Packed warp mode kernel: items are faces (every 4th (face, quadrant) item).
+// Whole-face warp mode kernel: every warp traces whole faces (small sources);
+// items are faces, face it being the quadrant-0 item items[4 it].  Up to 80
+// registers (measured faster than 64, where the loop spills); shared memory
+// bounds the warps per SM for these faces anyway.
 template <bool COLDENS>
-__global__ void __launch_bounds__(256, 4) k_trace_faces4_warp(TraceArgs a) {
+__global__ void __launch_bounds__(256, 3) k_trace_faces_whole_warp(TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (a.skip && *a.skip) return;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* my = smem_raw + (size_t)wid * face4_smem_bytes(a.hcap);
-  const int cap4 = 4 * (a.hcap + 1) * (a.hcap + 1);
+  unsigned char* my = smem_raw + (size_t)wid * whole_smem_bytes(a.hcap);
+  const int W = 2 * a.hcap + 1;
   double* buf = reinterpret_cast<double*>(my);
-  for (int t = lane; t < cap4; t += 32) buf[t] = 0.0;
+  for (int t = lane; t < W * W; t += 32) buf[t] = 0.0;  // one face buffer per warp
   __syncwarp();
   unsigned nrate = 0;
   for (;;) {
@@ -506,23 +574,24 @@ __global__ void __launch_bounds__(256, 4) k_trace_faces4_warp(TraceArgs a) {
     if (lane == 0) it = a.item_begin + atomicAdd(a.queue, 1);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= a.n_items) break;
-    trace_face4<32, COLDENS>(a, a.items[4 * it], lane, my, a.hcap, nrate);
+    trace_face_whole<32, COLDENS>(a, a.items[4 * it], lane, my, a.hcap, nrate);
     __syncwarp();
   }
   flush_rate_count(a, nrate);
 }
 
 // Kernel variant for (block, warps per CTA, coldens): block 128/256 = CTA mode,
-// 32 = warp mode and 4 = packed warp mode with wpb warps per CTA (1..8).  Null if
-// not instantiated.
+// 32 = warp mode and 4 = whole-face warp mode with wpb warps per CTA (1..8).  Null
+// if not instantiated.
 static const void* face_kernel(int block, int wpb, bool coldens) {
   switch (block) {
     case 32:
       if (wpb < 1 || wpb > 8) return nullptr;
       return coldens ? (const void*)k_trace_faces_warp<true> : (const void*)k_trace_faces_warp<false>;
-    case 4:  // packed warp mode (whole faces), wpb warps per CTA
+    case 4:  // whole-face warp mode, wpb warps per CTA
       if (wpb < 1 || wpb > 8) return nullptr;
-      return coldens ? (const void*)k_trace_faces4_warp<true> : (const void*)k_trace_faces4_warp<false>;
+      return coldens ? (const void*)k_trace_faces_whole_warp<true>
+                     : (const void*)k_trace_faces_whole_warp<false>;
     case 128: return coldens ? (const void*)k_trace_faces<128, true>
                              : (const void*)k_trace_faces<128, false>;
     case 256: return coldens ? (const void*)k_trace_faces<256, true>

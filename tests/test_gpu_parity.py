@@ -131,7 +131,7 @@ def test_lognormal_boxes_many_sources(n, nsrc, rmax, seed):
 
 
 # batched launch configurations (block_big, hsmall, hface): CTAs only (hsmall 0),
-# mixes of CTA, warp and packed-warp items, and warps for every item that fits
+# mixes of CTA, warp and whole-face-warp items, and warps for every item that fits
 SCHEDS = [(128, 0, 0), (256, 0, 0), (128, 11, 0), (256, 19, 13), (128, 24, 9), (128, 30, 20)]
 
 
