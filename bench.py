@@ -13,9 +13,16 @@ source-voxels with the paper's normaliser sum_s (4/3) pi R_s^3 (Sec. 4.2).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank traces its
-own independent box of the same size (weak scaling, no collective on the data
-path); value = all ranks' source-voxels / max-over-ranks time.
+Prints one JSON line (rank 0).  With N > 1 (torchrun, one rank per GPU) the
+one catalogue is sharded: rank r traces its longest-first share of the
+sources, the partial rate fields are summed with one NCCL all-reduce inside
+the timed step (the exchange of the paper's MPI mode, Sec. 3.2-3.3) and the
+chemistry runs on the sum on every rank; value = the catalogue's
+source-voxels / the slowest rank's step time (strong scaling).  Labelled
+extras (not the headline): the 128^3 / 1e4-source box (plain and batched),
+the 64-box ensemble in one launch, a rate-heavy variant (x_HI x 1e-4), the
+exact early exit, the RT <-> chemistry iteration as a CUDA graph and the
+adjoint's throughput.
 """
 import argparse
 import json
@@ -36,7 +43,7 @@ UNIT = "source-voxels/s"
 FP64_FLOPS_PER_SV = 9.0       # tau_in: 1 mul + 3 fma; tau_out: 1 fma
 FP64_FLOPS_PER_RATE = 10.0    # dtau*ds, 2 table fma, difference, 3 products
 BYTES_PER_SV = 16.0           # dtau gather (8 B) + rate read-modify-write share (8 B)
-SMS, FP64_FMA_PER_CLK_SM, SM_MAX_GHZ = 152, 2, 2.07
+FP64_FMA_PER_CLK_SM, SM_MAX_GHZ = 2, 2.07   # GB300: 2 DFMA lanes per SM-cycle, 2.07 GHz max
 
 
 def parse():
@@ -62,6 +69,11 @@ def parse():
                     help="sources of the gradient-throughput measurement (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--extras", type=int, default=1,
+                    help="1: also time the labelled extra workloads (128^3, ensemble, rate-heavy)")
+    ap.add_argument("--scratch", default=None,
+                    help="folder for the clock samples and the autotuner cache "
+                         "(default: a new temporary folder)")
     return ap.parse_args()
 
 
@@ -81,10 +93,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, folder):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.path = os.path.join(folder, "clocks_bench.csv")
 
     def start(self):
         try:
@@ -203,6 +215,77 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def flushed_trace_ms(g, gamma, flush, schedule="batched", reps=3):
+    """Median trace time (CUDA events of the library) over reps launches, L2 flushed."""
+    ts = []
+    for r in range(reps):
+        flush.fill_(float(r))
+        g.raytrace(gamma, schedule=schedule)
+        ts.append(g.stats()["trace_ms"])
+    return statistics.median(ts)
+
+
+def extra_box128(dev, flush, cache):
+    """128^3 / 100 Mpc, 1e4 sources at R = 32: batched and plain schedules."""
+    import torch
+    from paper_2311_01492_gb300 import api as A
+    from paper_2311_01492_gb300 import synth as S
+    w = S.box128_1e4()
+    f64 = dict(device=dev, dtype=torch.float64)
+    g = A.Grid(w["n"], w["cell_cm"])
+    g.set_tables("bb", T_bb=5e4)
+    g.set_density(torch.tensor(w["nH"].reshape(-1), **f64))
+    g.set_xHI(torch.tensor(w["xHI"].reshape(-1), **f64))
+    g.set_sources(torch.tensor(w["pos"], device=dev, dtype=torch.int32),
+                  torch.tensor(w["ndot"], **f64), torch.tensor(w["radius"], **f64))
+    tuned = g.autotune(cache)
+    gamma = torch.empty(w["n"] ** 3, **f64)
+    paper_sv = float(np.sum(4.0 / 3.0 * math.pi * w["radius"] ** 3))
+    tb = flushed_trace_ms(g, gamma, flush, "batched")
+    st = g.stats()
+    tp = flushed_trace_ms(g, gamma, flush, "plain", reps=2)
+    g.close()
+    return {"workload": "box128_100Mpc_lognormal_10000src_R32_bb5e4",
+            "source_voxels_paper": paper_sv, "source_voxels_exact": st["source_voxels"],
+            "rate_cells": st["rate_cells"], "schedule": "batched %s" % (tuned,),
+            "batched_ms": tb, "batched_sv_per_s": paper_sv / (tb * 1e-3),
+            "batched_ns_per_source_voxel": tb * 1e6 / paper_sv,
+            "plain_ms": tp, "plain_sv_per_s": paper_sv / (tp * 1e-3),
+            "plain_ns_per_source_voxel": tp * 1e6 / paper_sv, "batched_speedup": tp / tb}
+
+
+def extra_ensemble(dev, flush, cache):
+    """64 periodic boxes of 32..128^3 with 10..5000 sources each, one autotuned launch."""
+    import torch
+    from paper_2311_01492_gb300 import api as A
+    from paper_2311_01492_gb300 import synth as S
+    boxes = S.ensemble(64)
+    sizes = [b["n"] for b in boxes]
+    f64 = dict(device=dev, dtype=torch.float64)
+    g = A.Grid.ensemble(sizes, boxes[0]["cell_cm"])
+    g.set_tables("bb", T_bb=5e4)
+    g.set_density(torch.tensor(np.concatenate([b["nH"].reshape(-1) for b in boxes]), **f64))
+    g.set_xHI(torch.tensor(np.concatenate([b["xHI"].reshape(-1) for b in boxes]), **f64))
+    g.set_sources(torch.tensor(np.concatenate([b["pos"] for b in boxes]), device=dev,
+                               dtype=torch.int32),
+                  torch.tensor(np.concatenate([b["ndot"] for b in boxes]), **f64),
+                  torch.tensor(np.concatenate([b["radius"] for b in boxes]), **f64),
+                  torch.tensor(np.concatenate([np.full(len(b["pos"]), i) for i, b in
+                                               enumerate(boxes)]), device=dev, dtype=torch.int32))
+    tuned = g.autotune(cache)
+    gamma = torch.empty(sum(n ** 3 for n in sizes), **f64)
+    paper_sv = float(sum(np.sum(4.0 / 3.0 * math.pi * b["radius"] ** 3) for b in boxes))
+    t = flushed_trace_ms(g, gamma, flush, "batched")
+    st = g.stats()
+    g.close()
+    return {"workload": "ensemble64_32-128cubed_10-5000src_R5-50_bb5e4", "boxes": len(boxes),
+            "sources": int(sum(len(b["pos"]) for b in boxes)), "cells": int(sum(n ** 3 for n in sizes)),
+            "source_voxels_paper": paper_sv, "source_voxels_exact": st["source_voxels"],
+            "rate_cells": st["rate_cells"], "schedule": "batched, one launch %s" % (tuned,),
+            "trace_ms": t, "sv_per_s": paper_sv / (t * 1e-3),
+            "ns_per_source_voxel": t * 1e6 / paper_sv}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -211,6 +294,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    import tempfile
     import torch
     import torch.distributed as dist
     torch.cuda.set_device(local)
@@ -218,18 +302,25 @@ def main():
         dist.init_process_group("nccl")
     from paper_2311_01492_gb300 import api as A
     from paper_2311_01492_gb300 import _lib as L
+    from paper_2311_01492_gb300 import sharding as SH
 
-    w = workload(args, rank)
+    scratch = args.scratch or tempfile.mkdtemp(prefix="asora_bench_")
+    os.makedirs(scratch, exist_ok=True)
+    cache = os.path.join(scratch, "autotune_cache_rank%d.txt" % rank)
+    w = workload(args)  # one catalogue, sharded over the ranks
     n = w["n"]
     dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    pos, ndot, radius = SH.shard(w["pos"], w["ndot"], w["radius"], rank, world)
+    my_sv = float(np.sum(4.0 / 3.0 * math.pi * radius ** 3))
     g = A.Grid(n, w["cell_cm"])
     g.set_tables("bb", T_bb=5e4)
     f64 = dict(device=dev, dtype=torch.float64)
     nH_d = torch.tensor(w["nH"].reshape(-1), **f64)
     xHI_d = torch.tensor(w["xHI"].reshape(-1), **f64)
-    pos_d = torch.tensor(w["pos"], device=dev, dtype=torch.int32)
-    ndot_d = torch.tensor(w["ndot"], **f64)
-    R_d = torch.tensor(w["radius"], **f64)
+    pos_d = torch.tensor(pos, device=dev, dtype=torch.int32)
+    ndot_d = torch.tensor(ndot, **f64)
+    R_d = torch.tensor(radius, **f64)
     x0_d = (1.0 - xHI_d).contiguous()
     gamma = torch.empty(n ** 3, **f64)
     g.set_density(nH_d)
@@ -241,22 +332,24 @@ def main():
         tuned = (args.block, args.hsmall, args.hface)
         g.set_schedule(*tuned)
     else:
-        tuned = g.autotune(os.path.join(ROOT, "gpurun_out", "autotune_cache.txt")
-                           if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+        tuned = g.autotune(cache)
     stream = torch.cuda.current_stream()
 
-    def step():
+    def trace(gam):
         g.set_sources(pos_d, ndot_d, R_d)
-        g.raytrace(gamma, schedule="batched")
-        xa, xn, cnt = g.chemistry_step(gamma, x0_d, x0_d, dt)
-        return cnt
+        g.raytrace(gam, schedule="batched")
+
+    def chemistry(gam):
+        return g.chemistry_step(gam, x0_d, x0_d, dt)
+
+    step = SH.ShardedStep(trace, chemistry, dist, world)
 
     for _ in range(args.warmup):
-        step()
+        step(gamma)
     torch.cuda.synchronize()
 
     # ---------------- device-resident timed region
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local, scratch)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -268,7 +361,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step()
+        step(gamma)
         e1.record(stream)
         st = g.stats()  # synchronises; trace events were recorded on the launch stream
         torch.cuda.synchronize()
@@ -276,16 +369,16 @@ def main():
         trace_ms.append(st["trace_ms"])
         rate_cells.append(st["rate_cells"])
     launches = L.lib().rt_kernel_launch_count() - launches0
+    if world > 1:
+        dist.barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms, _ = SH.aggregate(ms, my_sv, dist, device=dev)
     st = g.stats()
     exact_sv = st["source_voxels"]
-    value = world * w["paper_sv"] / (ms * 1e-3)
+    value = w["paper_sv"] / (ms * 1e-3)  # the whole catalogue's source-voxels per step
     tr_ms = statistics.mean(trace_ms)
 
     # ---------------- plain (ASORA-style block-per-source) comparison
@@ -297,8 +390,8 @@ def main():
             g.raytrace(gamma, schedule="plain")
             pm.append(g.stats()["trace_ms"])
         pmed = statistics.median(pm)
-        plain = {"trace_ms": pmed, "sv_per_s": w["paper_sv"] / (pmed * 1e-3),
-                 "ns_per_source_voxel": pmed * 1e6 / w["paper_sv"],
+        plain = {"trace_ms": pmed, "sv_per_s": my_sv / (pmed * 1e-3),
+                 "ns_per_source_voxel": pmed * 1e6 / my_sv,
                  "batched_speedup": pmed / tr_ms}
 
     # ---------------- labelled extras (not the headline): the exact early exit, which
@@ -330,16 +423,44 @@ def main():
                "note": "graph capture and instantiation included; each iteration = dtau "
                        "precompute + batched trace + chemistry + convergence count"}
 
+    # ---------------- rate-heavy variant: the same field with x_HI x 1e-4 (a nearly
+    # ionised box as in the paper's Test 3), 1e5 of the sources: Gamma is non-zero over
+    # most traced cells, so the rate step and the FP64 atomics run on most cells
+    rate_heavy = None
+    if args.extras and rank == 0:
+        k = min(100_000, len(ndot))
+        rng = np.random.default_rng(13)
+        sel = np.sort(rng.choice(len(ndot), size=k, replace=False))
+        xlow = (xHI_d * 1e-4).contiguous()
+        g.set_xHI(xlow)
+        g.set_sources(pos_d[sel], ndot_d[sel], R_d[sel])
+        sv_sub = float(np.sum(4.0 / 3.0 * math.pi * radius[sel] ** 3))
+        th = flushed_trace_ms(g, gamma, flush, "batched")
+        sth = g.stats()
+        g.set_xHI(xHI_d)
+        tn = flushed_trace_ms(g, gamma, flush, "batched")
+        stn = g.stats()
+        rate_heavy = {"workload": "box250 field, x_HI x 1e-4, %d sources of the catalogue" % k,
+                      "source_voxels_paper": sv_sub, "source_voxels_exact": sth["source_voxels"],
+                      "trace_ms": th, "ns_per_source_voxel": th * 1e6 / sv_sub,
+                      "rate_cells": sth["rate_cells"],
+                      "rate_fraction": sth["rate_cells"] / sth["source_voxels"],
+                      "same_sources_opaque_trace_ms": tn,
+                      "same_sources_opaque_rate_fraction": stn["rate_cells"] / stn["source_voxels"],
+                      "note": "labelled extra: Gamma accumulated with one FP64 atomicAdd per "
+                              "non-zero (source, cell) term"}
+        g.set_sources(pos_d, ndot_d, R_d)
+
     # ---------------- adjoint: gradient throughput, 1e5 sources of the same box
     adjoint = None
-    if args.adjoint_src > 0:
-        k = min(args.adjoint_src, len(w["ndot"]))
+    if args.adjoint_src > 0 and rank == 0:
+        k = min(args.adjoint_src, len(ndot))
         rng = np.random.default_rng(11)
-        sel = np.sort(rng.choice(len(w["ndot"]), size=k, replace=False))
+        sel = np.sort(rng.choice(len(ndot), size=k, replace=False))
         psub, qsub, rsub = pos_d[sel], ndot_d[sel], R_d[sel]
         wl = torch.tensor(np.random.default_rng(2311_01492 + 4).standard_normal(n ** 3), **f64)
         g.set_sources(psub, qsub, rsub)
-        sv_sub = float(np.sum(4.0 / 3.0 * math.pi * w["radius"][sel] ** 3))
+        sv_sub = float(np.sum(4.0 / 3.0 * math.pi * radius[sel] ** 3))
         fw, bw, bwf = [], [], []
         for rep in range(3):
             flush.fill_(3.0)
@@ -365,13 +486,18 @@ def main():
                            "every layer"}
         g.set_sources(pos_d, ndot_d, R_d)
 
+    box128 = ensemble = None
+    if args.extras and rank == 0:
+        box128 = extra_box128(dev, flush, os.path.join(scratch, "autotune_box128.txt"))
+        ensemble = extra_ensemble(dev, flush, os.path.join(scratch, "autotune_ensemble.txt"))
+
     # ---------------- end to end through the public API with host buffers
     pin = dict(pin_memory=True)
     h_nH = torch.tensor(w["nH"].reshape(-1), dtype=torch.float64).pin_memory()
     h_xHI = torch.tensor(w["xHI"].reshape(-1), dtype=torch.float64).pin_memory()
-    h_pos = torch.tensor(w["pos"], dtype=torch.int32).pin_memory()
-    h_ndot = torch.tensor(w["ndot"], dtype=torch.float64).pin_memory()
-    h_R = torch.tensor(w["radius"], dtype=torch.float64).pin_memory()
+    h_pos = torch.tensor(pos, dtype=torch.int32).pin_memory()
+    h_ndot = torch.tensor(ndot, dtype=torch.float64).pin_memory()
+    h_R = torch.tensor(radius, dtype=torch.float64).pin_memory()
     h_gamma = torch.empty(n ** 3, dtype=torch.float64, **pin)
     h_cnt = torch.empty(1, dtype=torch.int64, **pin)
     e2e_in = [h_nH, h_xHI, h_pos, h_ndot, h_R]
@@ -384,7 +510,7 @@ def main():
     R2 = torch.empty_like(R_d)
     x02 = torch.empty_like(x0_d)
 
-    def e2e_step():
+    def e2e_trace(gam):
         nH2.copy_(h_nH, non_blocking=True)
         xHI2.copy_(h_xHI, non_blocking=True)
         pos2.copy_(h_pos, non_blocking=True)
@@ -393,32 +519,35 @@ def main():
         g.set_density(nH2)
         g.set_xHI(xHI2)
         g.set_sources(pos2, ndot2, R2)
-        g.raytrace(gamma, schedule="batched")
+        g.raytrace(gam, schedule="batched")
+
+    def e2e_chemistry(gam):
         torch.sub(1.0, xHI2, out=x02)
-        xa, xn, cnt = g.chemistry_step(gamma, x02, x02, dt)
-        h_gamma.copy_(gamma, non_blocking=True)
+        xa, xn, cnt = g.chemistry_step(gam, x02, x02, dt)
+        h_gamma.copy_(gam, non_blocking=True)
         h_cnt.copy_(cnt, non_blocking=True)
 
-    e2e_step()
+    e2e_step = SH.ShardedStep(e2e_trace, e2e_chemistry, dist, world)
+    e2e_step(gamma)
     torch.cuda.synchronize()
     e_ms = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(args.steps):
         flush.fill_(2.0)
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
-        e2e_step()
+        e2e_step(gamma)
         torch.cuda.synchronize()
         e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_ms = statistics.mean(e_ms)
     if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms, _ = SH.aggregate(e2e_ms, my_sv, dist, device=dev)
 
     # ---------------- roofline of the dominant kernel (the batched trace)
     flops = FP64_FLOPS_PER_SV * exact_sv + FP64_FLOPS_PER_RATE * statistics.mean(rate_cells)
     achieved_tf = flops / (tr_ms * 1e-3) / 1e12
-    peak_tf = SMS * FP64_FMA_PER_CLK_SM * 2 * SM_MAX_GHZ * 1e9 / 1e12
+    peak_tf = sms * FP64_FMA_PER_CLK_SM * 2 * SM_MAX_GHZ * 1e9 / 1e12
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -426,13 +555,15 @@ def main():
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     traffic = measured_traffic(exact_sv)
+    hbm_gbs = BYTES_PER_SV * exact_sv / (tr_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved_tf / peak_tf, "traffic": traffic,
-                "kernel": "k_trace_faces + k_trace_faces_warp + k_trace_faces_whole_warp (the batched trace; FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "kernel": "k_trace_faces + k_trace_faces_warp + k_trace_faces_whole_warp (the "
+                          "batched trace; FP64 pipe: %d SMs x 2 DFMA/clk x 2.07 GHz)" % sms,
                 "algorithmic_flops_per_launch": flops,
-                "hbm_view": {"achieved_gbs": BYTES_PER_SV * exact_sv / (tr_ms * 1e-3) / 1e9,
-                             "peak_gbs": hbm_peak,
-                             "frac": BYTES_PER_SV * exact_sv / (tr_ms * 1e-3) / 1e9 / hbm_peak,
+                "hbm_view": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak,
+                             "frac": hbm_gbs / hbm_peak,
+                             "target_frac": 0.5, "target_met": hbm_gbs / hbm_peak >= 0.5,
                              "peak_source": "MEASURED_PEAKS.json" if peaks else "fallback"}}
 
     cpu = None
@@ -457,30 +588,38 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
             "config": {"workload": w["name"], "n": n, "box_mpc": args.box_mpc,
                        "nsrc": len(w["ndot"]), "radius_cells": "5-50 (R=5(Ndot/1e50)^0.2)",
                        "schedule": "batched (persistent, 24 face-quadrant items/source, LPT "
                                    "queue; CTA %d threads, warp mode for layer half-width "
                                    "<= %d, whole faces per warp for <= %d)" % tuned,
-                       "step": "ingest + dtau + trace + chemistry",
+                       "step": "ingest + dtau + trace + chemistry"
+                               + (" (+ NCCL all-reduce of Gamma)" if world > 1 else ""),
                        "l2": "512 MB write between steps; fields 3 x 125 MB > L2",
-                       "per_rank": "independent box per rank (weak scaling)"},
+                       "parallelism": ("sources sharded longest-first over %d ranks, one "
+                                       "all-reduce(sum) of the 125 MB rate field per step"
+                                       % world) if world > 1 else "one GPU"},
             "ns_per_source_voxel": ms * 1e6 / w["paper_sv"],
             "source_voxels_paper": w["paper_sv"], "source_voxels_exact": exact_sv,
             "trace_only": {"ms": tr_ms, "ms_median": statistics.median(trace_ms),
-                           "sv_per_s": w["paper_sv"] / (tr_ms * 1e-3),
+                           "sv_per_s": my_sv / (tr_ms * 1e-3),
                            "sv_per_s_exact": exact_sv / (tr_ms * 1e-3),
-                           "ns_per_source_voxel": tr_ms * 1e6 / w["paper_sv"],
+                           "ns_per_source_voxel": tr_ms * 1e6 / my_sv,
                            "rate_cells": statistics.mean(rate_cells)},
             "plain": plain,
             "early_exit": early_exit,
             "iterate": iterate,
             "adjoint": adjoint,
+            "box128_1e4src": box128,
+            "ensemble64": ensemble,
+            "rate_heavy": rate_heavy,
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * w["paper_sv"] / (e2e_ms * 1e-3), "unit": UNIT,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "e2e": {"value": w["paper_sv"] / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                    "steps": args.steps},
             "gpu_launches": launches // max(1, args.steps),
             "gpu_launches_note": "library kernels per step (+ CUB radix-sort/scan kernels of the "
                                  "source ingest)",

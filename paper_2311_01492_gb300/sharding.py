@@ -47,3 +47,33 @@ def aggregate(ms_local, units_local, dist, device=None):
     dist.all_reduce(u, op=dist.ReduceOp.SUM)
     ms = float(t.item())
     return ms, float(u.item()) / (ms * 1e-3)
+
+
+def shard(pos, ndot, radius, rank, world):
+    """This rank's share of a source catalogue (the whole catalogue for world == 1)."""
+    if world <= 1:
+        return pos, ndot, radius
+    mine = lpt_shards(radius, world) == rank
+    return pos[mine], ndot[mine], radius[mine]
+
+
+class ShardedStep:
+    """One step of the sharded forward path on one rank: trace this rank's
+    sources into the rate field, sum the partial fields over the ranks (the
+    exchange step), then run the elementwise chemistry on the full field
+    (replicated on every rank).  ``trace(gamma)`` and ``chemistry(gamma)`` are
+    callables that fill / consume the rank's field; with one rank the sum is
+    skipped."""
+
+    def __init__(self, trace, chemistry, dist=None, world=1, group=None):
+        self.trace = trace
+        self.chemistry = chemistry
+        self.dist = dist
+        self.world = world
+        self.group = group
+
+    def __call__(self, gamma):
+        self.trace(gamma)
+        if self.world > 1:
+            sum_rates(gamma, self.dist, self.group)
+        return self.chemistry(gamma)

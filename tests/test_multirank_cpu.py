@@ -68,3 +68,64 @@ def test_lpt_shards_balance_work():
         loads = SH.shard_loads(R, owner, world)
         assert set(np.unique(owner)) == set(range(world))
         assert loads.max() / loads.mean() < 1.001
+
+
+def _bench_path_worker(rank, world, port, q):
+    """The sharded step bench.py runs, with the oracle as each rank's tracer."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import oracle as O
+    n = 16
+    w = S.lognormal_box(n, 10.0, 30, 1e50, 1e53, radius=None)
+    w["radius"] = np.minimum(w["radius"], 7.0)
+    pos, ndot, R = SH.shard(w["pos"], w["ndot"], w["radius"], rank, world)
+    tab = O.make_table("bb")
+    x0 = np.zeros(n ** 3)
+    dt = 5 * S.MYR_S
+
+    def trace(gamma):
+        gamma.copy_(torch.tensor(O.raytrace(n, w["cell_cm"], w["nH"], w["xHI"], pos, ndot, R,
+                                            tab)["gamma"]))
+
+    def chemistry(gamma):
+        return O.chemistry(w["nH"], x0, x0, gamma.numpy(), dt)
+
+    step = SH.ShardedStep(trace, chemistry, dist, world)
+    gamma = torch.zeros(n ** 3, dtype=torch.float64)
+    xa, xn, cnt = step(gamma)
+    if rank == 0:
+        full = O.raytrace(n, w["cell_cm"], w["nH"], w["xHI"], w["pos"], w["ndot"], w["radius"],
+                          tab)["gamma"]
+        xa_f, xn_f, cnt_f = O.chemistry(w["nH"], x0, x0, full, dt)
+        q.put((len(pos), gamma.numpy(), full, xn, xn_f, cnt, cnt_f))
+    else:
+        q.put((len(pos),))
+    dist.destroy_process_group()
+
+
+def test_bench_sharded_step_matches_single_rank():
+    """Each rank traces its longest-first share of the catalogue, the partial rate
+    fields are summed (the one exchange of the paper's MPI mode, Sec. 3.2-3.3) and
+    the chemistry runs on the sum: the same rates and ionised fractions as one rank
+    tracing every source."""
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_bench_path_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=300) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    r0 = [r for r in res if len(r) > 1][0]
+    nsrc_total = sum(r[0] for r in res)
+    assert nsrc_total == 30 and all(r[0] > 0 for r in res)
+    _, got, full, xn, xn_f, cnt, cnt_f = r0
+    nz = full != 0
+    assert np.array_equal(got != 0, nz)
+    np.testing.assert_allclose(got[nz], full[nz], rtol=1e-13)
+    np.testing.assert_allclose(xn, xn_f, rtol=1e-12, atol=1e-300)
+    assert abs(cnt - cnt_f) <= 1
