@@ -40,8 +40,12 @@ typedef enum {
   RT_ERR_INVALID = 1, /* bad argument or bad input data                       */
   RT_ERR_OOM = 2,     /* device allocation failed                             */
   RT_ERR_CUDA = 3,    /* a CUDA runtime call failed                           */
-  RT_ERR_TIMEOUT = 4, /* a bounded device-side wait ran out                   */
-  RT_ERR_STATE = 5    /* call order violated (e.g. trace before set_tables)   */
+  RT_ERR_TIMEOUT = 4, /* a bounded device-side wait ran out; no kernel of this version
+                         waits on the device, so it is not returned              */
+  RT_ERR_STATE = 5,   /* call order violated (e.g. trace before set_tables)   */
+  RT_ERR_BOUNDS = 6   /* a device-side capacity or bounds check failed: the trace that
+                         latched it is incomplete (reported by rt_check, rt_get_stats and
+                         the calls that synchronise)                              */
 } rt_status;
 
 typedef struct rt_grid* rt_grid_t;
@@ -127,7 +131,9 @@ rt_status rt_set_scale_factor(rt_grid_t g, double a);
  * ray-tracing radius in cells (> 0; cells with |Delta|^2 > floor(R^2) are not
  * traced, Sec. 3.3).  Sources in the same cell with the same radius are merged by
  * summing their rates (Sec. 3: identical spectra).  The library copies what it
- * needs; the pointers are not kept.  Synchronises the grid's stream. */
+ * needs; the pointers are not kept.  Synchronises the grid's stream.  On failure
+ * (RT_ERR_INVALID, RT_ERR_OOM, ...) the grid holds no sources until the next
+ * successful call (a trace then writes zero rates). */
 rt_status rt_set_sources(rt_grid_t g, int nsrc, const int32_t* d_pos, const int32_t* d_box,
                          const double* d_ndot, const double* d_radius);
 
@@ -219,8 +225,39 @@ rt_status rt_set_schedule(rt_grid_t g, int block_big, int hsmall, int hface);
 rt_status rt_autotune(rt_grid_t g, const char* cache_path, int* h_block, int* h_hsmall,
                       int* h_hface);
 
-/* Statistics of the last trace (synchronises the grid's stream). */
+/* Statistics of the last trace (synchronises the grid's stream).  Fills *out,
+ * then returns RT_ERR_BOUNDS if a kernel latched a failed device-side check
+ * since the last report (see rt_check). */
 rt_status rt_get_stats(rt_grid_t g, rt_stats* out);
+
+/* Device-side checks.  The trace kernels check their own capacities (layer
+ * width against the shared-memory buffers, layer index against the geometry
+ * table, source extent against the plain schedule's cube); a failed check
+ * skips the rest of that work item and latches an error bit in the grid
+ * instead of touching memory out of bounds.  Kernels run asynchronously, so
+ * rt_raytrace and rt_raytrace_backward return before such a bit can be seen:
+ * rt_check synchronises the grid's stream and returns RT_ERR_BOUNDS (and clears
+ * the bits) if any is latched, RT_OK otherwise.  rt_get_stats,
+ * rt_raytrace_source_coldens and rt_iterate with h_iters, which synchronise
+ * anyway, report the same. */
+rt_status rt_check(rt_grid_t g);
+
+/* Failure injection for tests: latches error bits (1 = layer capacity, 2 =
+ * geometry table, 4 = input data, 8 = plain-schedule cube) in the grid's
+ * device-side error word as a failed check would; no kernel runs.
+ * Synchronises.  RT_ERR_INVALID for other bit values. */
+rt_status rt_inject_device_error(rt_grid_t g, int bits);
+
+/* Process-wide cap on the device memory this library holds (all grids and
+ * scratch, every device), in bytes; 0 removes the cap.  The environment
+ * variable ASORA_DEVICE_MEMORY_LIMIT sets the initial cap.  An allocation that
+ * would exceed it fails as an out-of-memory would (RT_ERR_OOM), before calling
+ * cudaMalloc; the grid stays usable (see rt_set_sources for what a failed
+ * source ingest leaves).  Negative values: RT_ERR_INVALID. */
+rt_status rt_set_device_memory_limit(int64_t bytes);
+
+/* Device memory this library holds right now (bytes, all grids). */
+int64_t rt_device_memory_in_use(void);
 
 void rt_grid_destroy(rt_grid_t g);
 

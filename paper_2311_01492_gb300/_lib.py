@@ -5,11 +5,11 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libasora.so")
 
-RT_OK, RT_ERR_INVALID, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_TIMEOUT, RT_ERR_STATE = range(6)
+RT_OK, RT_ERR_INVALID, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_TIMEOUT, RT_ERR_STATE, RT_ERR_BOUNDS = range(7)
 RT_SCHED_AUTO, RT_SCHED_PLAIN, RT_SCHED_BATCHED, RT_SCHED_BATCHED_EXIT = 0, 1, 2, 3
 RT_TABLE_CHORDS, RT_TABLE_GREY_EXACT = 0, 1
 STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_OOM", 3: "RT_ERR_CUDA",
-                4: "RT_ERR_TIMEOUT", 5: "RT_ERR_STATE"}
+                4: "RT_ERR_TIMEOUT", 5: "RT_ERR_STATE", 6: "RT_ERR_BOUNDS"}
 
 
 class RtError(RuntimeError):
@@ -54,6 +54,10 @@ SIGNATURES = {
     "rt_chemistry_step": (_I, [_P, _P, _P, _P, _D, _D, _D, _D, _P, _P, _P]),
     "rt_iterate": (_I, [_P, _P, _D, _D, _D, _I, _D, _D, _I, _P, C.POINTER(_I)]),
     "rt_get_stats": (_I, [_P, C.POINTER(rt_stats)]),
+    "rt_check": (_I, [_P]),
+    "rt_inject_device_error": (_I, [_P, _I]),
+    "rt_set_device_memory_limit": (_I, [C.c_int64]),
+    "rt_device_memory_in_use": (C.c_int64, []),
     "rt_set_schedule": (_I, [_P, _I, _I, _I]),
     "rt_raytrace_backward": (_I, [_P, _P, _P, _P]),
     "rt_set_adjoint_mode": (_I, [_P, _I]),

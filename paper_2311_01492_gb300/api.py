@@ -51,6 +51,15 @@ def table_blackbody(T_bb=5e4, beta=2.8, E0=TABLE_E0, E1=TABLE_E1, bits=TABLE_BIT
     return g, h
 
 
+def set_device_memory_limit(nbytes):
+    """Process-wide cap on the device memory the library holds (0: none)."""
+    L.check(L.lib().rt_set_device_memory_limit(int(nbytes)), "rt_set_device_memory_limit")
+
+
+def device_memory_in_use():
+    return int(L.lib().rt_device_memory_in_use())
+
+
 def shell_enumerate(q):
     n = L.lib().rt_shell_enumerate(q, None)
     if n < 0:
@@ -219,6 +228,10 @@ class Grid:
         s = L.rt_stats()
         L.check(self._lib.rt_get_stats(self._h, C.byref(s)), "rt_get_stats")
         return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def check(self):
+        """Synchronise and raise RtError(RT_ERR_BOUNDS) if a device-side check failed."""
+        L.check(self._lib.rt_check(self._h), "rt_check")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -3,9 +3,12 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <fstream>
+#include <mutex>
 #include <sstream>
 #include <string>
+#include <unordered_map>
 
 #include "asora_internal.cuh"
 
@@ -15,6 +18,52 @@ static thread_local std::string g_last_error;
 static std::atomic<long long> g_launches{0};
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------- device memory
+static std::mutex g_mem_mutex;
+static std::unordered_map<void*, size_t> g_mem_sizes;
+static int64_t g_mem_live = 0;
+static int64_t g_mem_limit = -1;  // -1: not read yet, 0: no limit
+
+static int64_t mem_limit_locked() {
+  if (g_mem_limit < 0) {
+    g_mem_limit = 0;
+    if (const char* v = std::getenv("ASORA_DEVICE_MEMORY_LIMIT")) {
+      char* end = nullptr;
+      const long long x = std::strtoll(v, &end, 10);
+      if (end != v && x > 0) g_mem_limit = x;
+    }
+  }
+  return g_mem_limit;
+}
+
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+  *p = nullptr;
+  std::lock_guard<std::mutex> lk(g_mem_mutex);
+  const int64_t lim = mem_limit_locked();
+  if (lim > 0 && g_mem_live + (int64_t)bytes > lim) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  g_mem_sizes[*p] = bytes;
+  g_mem_live += (int64_t)bytes;
+  return cudaSuccess;
+}
+
+cudaError_t dev_free(void* p) {
+  if (!p) return cudaSuccess;
+  {
+    std::lock_guard<std::mutex> lk(g_mem_mutex);
+    auto it = g_mem_sizes.find(p);
+    if (it != g_mem_sizes.end()) {
+      g_mem_live -= (int64_t)it->second;
+      g_mem_sizes.erase(it);
+    }
+  }
+  return cudaFree(p);
+}
 
 rt_status fail(rt_status st, const std::string& msg) {
   g_last_error = msg;
@@ -36,13 +85,13 @@ static int isqrt_h(int64_t x) {
 }
 
 static void free_grid(Grid* g) {
-  cudaFree(g->boxes_d); cudaFree(g->gtab); cudaFree(g->htab);
-  cudaFree(g->dtau); cudaFree(g->dtauT); cudaFree(g->invn);
+  dev_free(g->boxes_d); dev_free(g->gtab); dev_free(g->htab);
+  dev_free(g->dtau); dev_free(g->dtauT); dev_free(g->invn);
   free_sources(*g);
-  cudaFree(g->geo); cudaFree(g->georow); cudaFree(g->queue); cudaFree(g->err);
-  cudaFree(g->cube); cudaFree(g->unconv); cudaFree(g->xbuf); cudaFree(g->xavg);
-  cudaFree(g->xavg2); cudaFree(g->xhi_int); cudaFree(g->flags); cudaFree(g->counters);
-  cudaFree(g->bwd_stack); cudaFree(g->dq_merged);
+  dev_free(g->geo); dev_free(g->georow); dev_free(g->queue); dev_free(g->err);
+  dev_free(g->cube); dev_free(g->unconv); dev_free(g->xbuf); dev_free(g->xavg);
+  dev_free(g->xavg2); dev_free(g->xhi_int); dev_free(g->flags); dev_free(g->counters);
+  dev_free(g->bwd_stack); dev_free(g->dq_merged);
   free_row_tables(*g);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
@@ -67,16 +116,16 @@ static rt_status ensure_geometry(Grid& g, int mmax) {
   if (mmax <= g.geo_mmax) return RT_OK;
   GeoEntry* geo = nullptr;
   GeoRow* georow = nullptr;
-  TRY(cudaMalloc(&geo, geo_count(mmax) * sizeof(GeoEntry)));
-  cudaError_t e = cudaMalloc(&georow, georow_count(mmax) * sizeof(GeoRow));
+  TRY(dev_malloc(&geo, geo_count(mmax) * sizeof(GeoEntry)));
+  cudaError_t e = dev_malloc(&georow, georow_count(mmax) * sizeof(GeoRow));
   if (e == cudaSuccess) e = launch_geometry(geo, georow, mmax, g.stream);
   if (e != cudaSuccess) {
-    cudaFree(geo);
-    cudaFree(georow);
+    dev_free(geo);
+    dev_free(georow);
     return cuda_fail(e, "geometry");
   }
-  cudaFree(g.geo);
-  cudaFree(g.georow);
+  dev_free(g.geo);
+  dev_free(g.georow);
   g.geo = geo;
   g.georow = georow;
   g.geo_mmax = mmax;
@@ -142,6 +191,22 @@ static TraceArgs base_args(Grid& g) {
   return a;
 }
 
+// Error bits latched by the kernels since the last check (the caller has
+// synchronised the grid's stream); clears them.
+static rt_status latched_errors(Grid& g) {
+  int herr = 0;
+  TRY(cudaMemcpy(&herr, g.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!herr) return RT_OK;
+  TRY(cudaMemset(g.err, 0, sizeof(int)));
+  std::string what;
+  if (herr & ERR_LAYER_CAP) what += " layer wider than the shared-memory capacity;";
+  if (herr & ERR_GEO) what += " layer beyond the geometry table;";
+  if (herr & ERR_CUBE) what += " source extent beyond the plain schedule's cube;";
+  if (herr & ERR_INPUT) what += " invalid input data;";
+  return fail(RT_ERR_BOUNDS, "device-side check failed (error bits " + std::to_string(herr) +
+                                 "):" + what + " the results of the last trace are incomplete");
+}
+
 static rt_status check_ready(Grid& g, const char* who) {
   if (!g.have_tables) return fail(RT_ERR_STATE, std::string(who) + ": rt_set_tables not called");
   if (!g.nH) return fail(RT_ERR_STATE, std::string(who) + ": rt_set_density not called");
@@ -170,10 +235,10 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
     const size_t side = 2 * (size_t)E + 1;
     const size_t need = side * side * side * sizeof(double) * (size_t)grid;
     if (need > g.cube_bytes) {
-      cudaFree(g.cube);
+      dev_free(g.cube);
       g.cube = nullptr;
       g.cube_bytes = 0;
-      TRY(cudaMalloc(&g.cube, need));
+      TRY(dev_malloc(&g.cube, need));
       g.cube_bytes = need;
     }
     a.scratch = g.cube;
@@ -327,17 +392,17 @@ rt_status rt_ensemble_create(rt_grid_t* out, int nbox, const int* h_n, const dou
   }
   g->ncell = off;
   cudaError_t e = cudaSuccess;
-  e = cudaMalloc(&g->boxes_d, nbox * sizeof(BoxDev));
+  e = dev_malloc(&g->boxes_d, nbox * sizeof(BoxDev));
   if (e == cudaSuccess) e = cudaMemcpy(g->boxes_d, g->boxes_h.data(), nbox * sizeof(BoxDev), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&g->dtau, g->ncell * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&g->dtauT, g->ncell * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&g->invn, g->ncell * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&g->queue, 64 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&g->err, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&g->unconv, 16 * sizeof(int64_t));
-  if (e == cudaSuccess) e = cudaMalloc(&g->flags, 16 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&g->counters, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = dev_malloc(&g->dtau, g->ncell * sizeof(double));
+  if (e == cudaSuccess) e = dev_malloc(&g->dtauT, g->ncell * sizeof(double));
+  if (e == cudaSuccess) e = dev_malloc(&g->invn, g->ncell * sizeof(double));
+  if (e == cudaSuccess) e = dev_malloc(&g->queue, 64 * sizeof(int));
+  if (e == cudaSuccess) e = dev_malloc(&g->err, 2 * sizeof(int));  // [0] traces, [1] validation
+  if (e == cudaSuccess) e = cudaMemset(g->err, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = dev_malloc(&g->unconv, 16 * sizeof(int64_t));
+  if (e == cudaSuccess) e = dev_malloc(&g->flags, 16 * sizeof(int));
+  if (e == cudaSuccess) e = dev_malloc(&g->counters, 8 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(g->counters, 0, 8 * sizeof(unsigned long long));
   for (auto& ev : g->ev)
     if (e == cudaSuccess) e = cudaEventCreate(&ev);
@@ -391,17 +456,17 @@ rt_status rt_set_tables(rt_grid_t h, int kind, int E0, int E1, int bits, const d
     }
   }
   double2 *dg = nullptr, *dh = nullptr;
-  TRY(cudaMalloc(&dg, S * sizeof(double2)));
-  cudaError_t e = cudaMalloc(&dh, S * sizeof(double2));
+  TRY(dev_malloc(&dg, S * sizeof(double2)));
+  cudaError_t e = dev_malloc(&dh, S * sizeof(double2));
   if (e == cudaSuccess) e = cudaMemcpy(dg, gc.data(), S * sizeof(double2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(dh, hc.data(), S * sizeof(double2), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
-    cudaFree(dg);
-    cudaFree(dh);
+    dev_free(dg);
+    dev_free(dh);
     return cuda_fail(e, "rt_set_tables");
   }
-  cudaFree(g.gtab);
-  cudaFree(g.htab);
+  dev_free(g.gtab);
+  dev_free(g.htab);
   g.gtab = dg;
   g.htab = dh;
   g.tab_kind = kind;
@@ -418,9 +483,9 @@ static rt_status set_field(rt_grid_t h, const double* d, bool density) {
   if (!d) return fail(RT_ERR_INVALID, std::string(who) + ": null field");
   Grid& g = *reinterpret_cast<Grid*>(h);
   int herr = 0;
-  TRY(cudaMemsetAsync(g.err, 0, sizeof(int), g.stream));
+  TRY(cudaMemsetAsync(g.err + 1, 0, sizeof(int), g.stream));
   TRY(launch_validate_fields(g, density ? d : nullptr, density ? nullptr : d));
-  TRY(cudaMemcpyAsync(&herr, g.err, sizeof(int), cudaMemcpyDeviceToHost, g.stream));
+  TRY(cudaMemcpyAsync(&herr, g.err + 1, sizeof(int), cudaMemcpyDeviceToHost, g.stream));
   TRY(cudaStreamSynchronize(g.stream));
   if (herr)
     return fail(RT_ERR_INVALID, density ? "rt_set_density: n_H must be finite, >= +0 and <= 1e12"
@@ -454,11 +519,19 @@ rt_status rt_set_sources(rt_grid_t h, int nsrc, const int32_t* d_pos, const int3
     return fail(RT_ERR_INVALID, "rt_set_sources: null source array");
   Grid& g = *reinterpret_cast<Grid*>(h);
   rt_status st = ingest_sources(g, nsrc, d_pos, d_box, d_ndot, d_radius);
-  if (st != RT_OK) return st;
-  const int mmax = std::max(1, std::min(isqrt_h(g.max_r2), g.nmax / 2 + 1));
-  st = ensure_geometry(g, mmax);
-  if (st != RT_OK) return st;
-  return ensure_row_tables(g);
+  if (st == RT_OK) {
+    const int mmax = std::max(1, std::min(isqrt_h(g.max_r2), g.nmax / 2 + 1));
+    st = ensure_geometry(g, mmax);
+  }
+  if (st == RT_OK) st = ensure_row_tables(g);
+  if (st != RT_OK) {  // no kernel may use sources whose geometry or tables are missing
+    g.nsrc = 0;
+    g.nsrc_in = 0;
+    g.max_r2 = 0;
+    g.source_voxels = 0;
+    g.r2_sorted_h.clear();
+  }
+  return st;
 }
 
 rt_status rt_raytrace(rt_grid_t h, double* d_gamma, int schedule) {
@@ -517,7 +590,7 @@ rt_status rt_raytrace_source_coldens(rt_grid_t h, int src, double* d_coldens, in
   }
   if (st != RT_OK) return st;
   TRY(cudaStreamSynchronize(g.stream));  // hitems is a stack buffer
-  return RT_OK;
+  return latched_errors(g);
 }
 
 rt_status rt_get_stats(rt_grid_t h, rt_stats* out) {
@@ -534,13 +607,40 @@ rt_status rt_get_stats(rt_grid_t h, rt_stats* out) {
   g.stats.kernel_launches = g_launches.load();
   g.stats.row_table_bytes = g.rtab ? g.rtab_bytes + g.itab_bytes : 0;
   *out = g.stats;
-  int herr = 0;
-  TRY(cudaMemcpy(&herr, g.err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (herr) {
-    cudaMemset(g.err, 0, sizeof(int));
-    return fail(RT_ERR_CUDA, "device-side bounds check failed (error bits " + std::to_string(herr) + ")");
-  }
+  return latched_errors(g);
+}
+
+rt_status rt_check(rt_grid_t h) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_check: null grid");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  TRY(cudaStreamSynchronize(g.stream));
+  return latched_errors(g);
+}
+
+rt_status rt_inject_device_error(rt_grid_t h, int bits) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_inject_device_error: null grid");
+  if (bits <= 0 || bits > (ERR_LAYER_CAP | ERR_GEO | ERR_INPUT | ERR_CUBE))
+    return fail(RT_ERR_INVALID, "rt_inject_device_error: unknown error bits");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  int cur = 0;
+  TRY(cudaStreamSynchronize(g.stream));
+  TRY(cudaMemcpy(&cur, g.err, sizeof(int), cudaMemcpyDeviceToHost));
+  cur |= bits;
+  TRY(cudaMemcpy(g.err, &cur, sizeof(int), cudaMemcpyHostToDevice));
   return RT_OK;
+}
+
+rt_status rt_set_device_memory_limit(int64_t bytes) {
+  if (bytes < 0) return fail(RT_ERR_INVALID, "rt_set_device_memory_limit: negative limit");
+  std::lock_guard<std::mutex> lk(g_mem_mutex);
+  mem_limit_locked();  // the environment's value is replaced, not read later
+  g_mem_limit = bytes;
+  return RT_OK;
+}
+
+int64_t rt_device_memory_in_use(void) {
+  std::lock_guard<std::mutex> lk(g_mem_mutex);
+  return g_mem_live;
 }
 
 rt_status rt_chemistry_step(rt_grid_t h, const double* d_gamma, const double* d_x0,
@@ -572,10 +672,10 @@ rt_status rt_iterate(rt_grid_t h, double* d_x, double dt_s, double alpha_H, doub
   if (!g.nH) return fail(RT_ERR_STATE, "rt_iterate: rt_set_density not called");
   const size_t bytes = g.ncell * sizeof(double);
   if (!g.xbuf) {
-    TRY(cudaMalloc(&g.xbuf, bytes));
-    TRY(cudaMalloc(&g.xavg, bytes));
-    TRY(cudaMalloc(&g.xavg2, bytes));
-    TRY(cudaMalloc(&g.xhi_int, bytes));
+    TRY(dev_malloc(&g.xbuf, bytes));
+    TRY(dev_malloc(&g.xavg, bytes));
+    TRY(dev_malloc(&g.xavg2, bytes));
+    TRY(dev_malloc(&g.xhi_int, bytes));
   }
   g.xHI = g.xhi_int;
   const int64_t limit = (int64_t)std::ceil(conv_frac * (double)g.ncell);
@@ -649,6 +749,7 @@ rt_status rt_iterate(rt_grid_t h, double* d_x, double dt_s, double alpha_H, doub
     TRY(cudaStreamSynchronize(user));
     iters = fl[1];
     *h_iters = iters;
+    return latched_errors(g);
   }
   return RT_OK;
 }
@@ -667,10 +768,10 @@ rt_status rt_raytrace_backward(rt_grid_t h, const double* d_dL_dgamma, double* d
   TRY(cudaMemsetAsync(d_dL_dlog_nHI, 0, g.ncell * sizeof(double), g.stream));
   if (g.nsrc == 0) return RT_OK;
   if (g.dq_cap < g.nsrc) {
-    cudaFree(g.dq_merged);
+    dev_free(g.dq_merged);
     g.dq_merged = nullptr;
     g.dq_cap = 0;
-    TRY(cudaMalloc(&g.dq_merged, g.nsrc * sizeof(double)));
+    TRY(dev_malloc(&g.dq_merged, g.nsrc * sizeof(double)));
     g.dq_cap = g.nsrc;
   }
   TRY(cudaMemsetAsync(g.dq_merged, 0, g.nsrc * sizeof(double), g.stream));
@@ -711,10 +812,10 @@ rt_status rt_raytrace_backward(rt_grid_t h, const double* d_dL_dgamma, double* d
   }
   const size_t need = (cap_c * (size_t)grid_c + cap_w * (size_t)grid_w * 8) * sizeof(double2);
   if (need > g.bwd_stack_bytes) {
-    cudaFree(g.bwd_stack);
+    dev_free(g.bwd_stack);
     g.bwd_stack = nullptr;
     g.bwd_stack_bytes = 0;
-    TRY(cudaMalloc(&g.bwd_stack, need));
+    TRY(dev_malloc(&g.bwd_stack, need));
     g.bwd_stack_bytes = need;
   }
   TraceArgs a = base_args(g);
@@ -818,7 +919,7 @@ rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_
     return RT_OK;
   }
   double* gam = nullptr;
-  TRY(cudaMalloc(&gam, g.ncell * sizeof(double)));
+  TRY(dev_malloc(&gam, g.ncell * sizeof(double)));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -868,14 +969,14 @@ rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaFree(gam);
+  dev_free(gam);
   if (st != RT_OK) return st;
   g.hface = bf;
   // stage 3: the paper's block-per-source schedule against the tuned batched one
   // (RT_SCHED_AUTO then takes the faster)
   if (st == RT_OK) {
     float tp = 0.f;
-    TRY(cudaMalloc(&gam, g.ncell * sizeof(double)));
+    TRY(dev_malloc(&gam, g.ncell * sizeof(double)));
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, g.stream);
@@ -885,7 +986,7 @@ rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_
     cudaEventElapsedTime(&tp, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(gam);
+    dev_free(gam);
     if (st != RT_OK) return st;
     g.auto_plain = tp < best ? 1 : 0;
   }

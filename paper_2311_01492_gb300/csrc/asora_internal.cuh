@@ -226,6 +226,17 @@ struct Grid {
 // Kernels launched by this library in this process (host-side count).
 void count_launch(int n = 1);
 
+// Device allocations of the library: cudaMalloc/cudaFree with a process-wide
+// cap on the bytes held (rt_set_device_memory_limit, or the environment
+// variable ASORA_DEVICE_MEMORY_LIMIT); an allocation beyond the cap fails with
+// cudaErrorMemoryAllocation (RT_ERR_OOM) without calling cudaMalloc.
+cudaError_t dev_malloc_raw(void** p, size_t bytes);
+cudaError_t dev_free(void* p);
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+
 // Frees the source arrays and the ingest scratch (prep.cu).
 void free_sources(Grid& g);
 

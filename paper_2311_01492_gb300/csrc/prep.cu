@@ -13,6 +13,8 @@
 namespace asora {
 
 // ----------------------------------------------------------- validation
+// (writes its own error word, g.err[1], so that it never clears the bits the
+// trace kernels latch in g.err[0])
 __global__ void k_validate_fields(const BoxDev* __restrict__ boxes, int nbox,
                                   const double* __restrict__ nH, const double* __restrict__ xHI,
                                   int64_t ncell, int* __restrict__ err) {
@@ -32,7 +34,7 @@ __global__ void k_validate_fields(const BoxDev* __restrict__ boxes, int nbox,
 }
 
 cudaError_t launch_validate_fields(Grid& g, const double* nH, const double* xHI) {
-  k_validate_fields<<<1024, 256, 0, g.stream>>>(g.boxes_d, g.nbox, nH, xHI, g.ncell, g.err);
+  k_validate_fields<<<1024, 256, 0, g.stream>>>(g.boxes_d, g.nbox, nH, xHI, g.ncell, g.err + 1);
   count_launch();
   return cudaGetLastError();
 }
@@ -273,15 +275,15 @@ static int64_t ball_count(int r2, int n) {
 
 void free_sources(Grid& g) {
   Grid::Ingest& w = g.ing;
-  cudaFree(g.src); cudaFree(g.ndot); cudaFree(g.r2lim); cudaFree(g.items);
-  cudaFree(g.src_of_input); cudaFree(g.ndot_in);
+  dev_free(g.src); dev_free(g.ndot); dev_free(g.r2lim); dev_free(g.items);
+  dev_free(g.src_of_input); dev_free(g.ndot_in);
   g.src = nullptr; g.ndot = nullptr; g.r2lim = nullptr; g.items = nullptr;
   g.src_of_input = nullptr; g.ndot_in = nullptr;
   g.src_cap = 0;
-  cudaFree(w.keys); cudaFree(w.keys2); cudaFree(w.idx); cudaFree(w.idx2); cudaFree(w.r2in);
-  cudaFree(w.head); cudaFree(w.mid); cudaFree(w.msrc); cudaFree(w.mndot); cudaFree(w.mr2);
-  cudaFree(w.lkey); cudaFree(w.lkey2); cudaFree(w.lval); cudaFree(w.order); cudaFree(w.lpt);
-  cudaFree(w.tmp); cudaFree(w.dscal);
+  dev_free(w.keys); dev_free(w.keys2); dev_free(w.idx); dev_free(w.idx2); dev_free(w.r2in);
+  dev_free(w.head); dev_free(w.mid); dev_free(w.msrc); dev_free(w.mndot); dev_free(w.mr2);
+  dev_free(w.lkey); dev_free(w.lkey2); dev_free(w.lval); dev_free(w.order); dev_free(w.lpt);
+  dev_free(w.tmp); dev_free(w.dscal);
   cudaFreeHost(w.hscal); cudaFreeHost(w.r2pin); cudaFreeHost(w.srcpin);
   w = Grid::Ingest{};
 }
@@ -294,7 +296,7 @@ static cudaError_t reserve_sources(Grid& g, size_t n) {
   free_sources(g);
   cudaError_t e = cudaSuccess;
   auto dm = [&](auto*& p, size_t bytes) {
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p), bytes);
+    if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void**>(&p), bytes);
   };
   dm(w.keys, n * sizeof(uint64_t)); dm(w.keys2, n * sizeof(uint64_t));
   dm(w.idx, n * sizeof(int)); dm(w.idx2, n * sizeof(int)); dm(w.r2in, n * sizeof(int));
@@ -349,9 +351,9 @@ rt_status ingest_sources(Grid& g, int nsrc, const int32_t* d_pos, const int32_t*
   if (nsrc == 0) return RT_OK;
   CK(reserve_sources(g, (size_t)nsrc));
 
-  CK(cudaMemsetAsync(g.err, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(g.err + 1, 0, sizeof(int), s));  // the validation word, not the trace's
   k_src_keys<<<nb, T, 0, s>>>(g.boxes_d, g.nbox, nsrc, d_pos, d_box, d_ndot, d_radius, w.keys,
-                              w.idx, w.r2in, g.err);
+                              w.idx, w.r2in, g.err + 1);
   count_launch();
   CK(cudaGetLastError());
   // stable sort by (cell, r2): co-located sources with equal radius become adjacent
@@ -365,7 +367,7 @@ rt_status ingest_sources(Grid& g, int nsrc, const int32_t* d_pos, const int32_t*
   CK(cub::DeviceScan::ExclusiveSum(w.tmp, need, w.head, w.mid, nsrc, s));
   need = w.tmp_bytes;
   CK(cub::DeviceReduce::Max(w.tmp, need, w.r2in, w.dscal, nsrc, s));  // for the LPT key
-  CK(cudaMemcpyAsync(w.hscal + 0, g.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(w.hscal + 0, g.err + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(w.hscal + 1, w.head + nsrc - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(w.hscal + 2, w.mid + nsrc - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(w.hscal + 3, w.dscal, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -517,8 +519,8 @@ __global__ void k_interior_tables(const int* __restrict__ ent_r2, const int* __r
 }
 
 void free_row_tables(Grid& g) {
-  cudaFree(g.rtab); cudaFree(g.rtab_off); cudaFree(g.rtab_first); cudaFree(g.rtab_hcap);
-  cudaFree(g.rtab_slot); cudaFree(g.itab); cudaFree(g.itab_off);
+  dev_free(g.rtab); dev_free(g.rtab_off); dev_free(g.rtab_first); dev_free(g.rtab_hcap);
+  dev_free(g.rtab_slot); dev_free(g.itab); dev_free(g.itab_off);
   g.rtab = nullptr; g.rtab_off = g.rtab_first = g.rtab_hcap = g.rtab_slot = nullptr;
   g.itab = nullptr; g.itab_off = nullptr;
   g.itab_bytes = 0;
@@ -591,16 +593,16 @@ rt_status ensure_row_tables(Grid& g) {
       goto fail;                                \
     }                                           \
   } while (0)
-  CK(cudaMalloc(&g.rtab, std::max<int64_t>(cur, 16)));
-  CK(cudaMalloc(&g.rtab_off, off.size() * sizeof(int)));
-  CK(cudaMalloc(&g.rtab_first, first.size() * sizeof(int)));
-  CK(cudaMalloc(&g.rtab_hcap, hcap.size() * sizeof(int)));
-  CK(cudaMalloc(&g.rtab_slot, slot.size() * sizeof(int)));
-  CK(cudaMalloc(&g.itab, std::max<int64_t>(icur, 16)));
-  CK(cudaMalloc(&g.itab_off, ioff.size() * sizeof(int)));
+  CK(dev_malloc(&g.rtab, std::max<int64_t>(cur, 16)));
+  CK(dev_malloc(&g.rtab_off, off.size() * sizeof(int)));
+  CK(dev_malloc(&g.rtab_first, first.size() * sizeof(int)));
+  CK(dev_malloc(&g.rtab_hcap, hcap.size() * sizeof(int)));
+  CK(dev_malloc(&g.rtab_slot, slot.size() * sizeof(int)));
+  CK(dev_malloc(&g.itab, std::max<int64_t>(icur, 16)));
+  CK(dev_malloc(&g.itab_off, ioff.size() * sizeof(int)));
   CK(cudaMemcpyAsync(g.itab_off, ioff.data(), ioff.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  CK(cudaMalloc(&d_r2, std::max(nent, 1) * sizeof(int)));
-  CK(cudaMalloc(&d_m, std::max(nent, 1) * sizeof(int)));
+  CK(dev_malloc(&d_r2, std::max(nent, 1) * sizeof(int)));
+  CK(dev_malloc(&d_m, std::max(nent, 1) * sizeof(int)));
   CK(cudaMemcpyAsync(g.rtab_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(g.rtab_first, first.data(), first.size() * sizeof(int),
                      cudaMemcpyHostToDevice, s));
@@ -617,8 +619,8 @@ rt_status ensure_row_tables(Grid& g) {
     CK(cudaGetLastError());
   }
   CK(cudaStreamSynchronize(s));  // host vectors go out of scope
-  cudaFree(d_r2);
-  cudaFree(d_m);
+  dev_free(d_r2);
+  dev_free(d_m);
   g.rtab_max_r2 = maxv;
   g.rtab_bytes = cur;
   g.itab_bytes = icur;
@@ -627,8 +629,8 @@ rt_status ensure_row_tables(Grid& g) {
   return RT_OK;
 fail:
   cudaStreamSynchronize(s);
-  cudaFree(d_r2);
-  cudaFree(d_m);
+  dev_free(d_r2);
+  dev_free(d_m);
   free_row_tables(g);
   return st;
 #undef CK

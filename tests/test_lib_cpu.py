@@ -68,3 +68,11 @@ def test_argument_errors_without_a_gpu(lib):
     assert lib.rt_table_nknots(30, 14, 6) == 44 * 64 + 2
     assert lib.rt_table_nknots(0, 14, 6) == -1
     assert lib.rt_shell_enumerate(-1, None) == -1
+
+
+def test_device_memory_limit_argument_checks_need_no_gpu(lib):
+    from paper_2311_01492_gb300 import _lib
+    assert lib.rt_set_device_memory_limit(-1) == _lib.RT_ERR_INVALID
+    assert b"negative" in lib.rt_last_error()
+    assert lib.rt_device_memory_in_use() == 0  # nothing allocated without a GPU
+    assert lib.rt_set_device_memory_limit(0) == _lib.RT_OK
