@@ -24,6 +24,13 @@
 //    make the scheme exact on axes and grid diagonals (Sec. 3.1, last
 //    paragraph).  tau_in = fma(w4,c4, fma(w3,c3, fma(w2,c2, w1*c1))).
 //    Path length ds = sqrt(1 + (Delta_p1^2 + Delta_p2^2)/Delta_d^2)  (Sec. 3.1).
+//    Optional optical-depth-modulated weights (interp_mode 1; the C2Ray paper's
+//    App. A, which Sec. 3.1 cites for the weighting but does not print): each
+//    weight is multiplied by m_n = 1/max(tau_n, tau_w0), tau_n the optical depth
+//    at threshold out of interpolant n, and the sum is normalised:
+//    w'_n = w_n*m_n, S = ((w'_1+w'_2)+w'_3)+w'_4,
+//    tau_in = fma(w'4,c4, fma(w'3,c3, fma(w'2,c2, w'1*c1))) / S.  The default
+//    (interp_mode 0) is the paper's geometric weighting.
 //    tau_out = fma(dtau(p), ds, tau_in).
 //    Source voxel (q = 0, "treated directly", Sec. 3.3): tau_in = 0,
 //    tau_out = dtau(s)/2.  Voxels with max|Delta| = 1 (their only non-zero
@@ -74,6 +81,7 @@ inline double re(double x) { return x; }
 inline double re(const cplx& x) { return x.real(); }
 inline double fmaT(double a, double b, double c) { return std::fma(a, b, c); }
 inline cplx fmaT(double a, const cplx& b, const cplx& c) { return a * b + c; }
+inline cplx fmaT(const cplx& a, const cplx& b, const cplx& c) { return a * b + c; }
 inline double expT(double x) { return std::exp(x); }
 inline cplx expT(const cplx& x) { return std::exp(x); }
 
@@ -139,6 +147,8 @@ struct Params {
   double cell_cm;
   double sigma0;
   double tau_lim;
+  int interp = 0;        // 0: geometric weights; 1: optical-depth-modulated weights
+  double tau_w0 = 0.6;   // floor of tau_n in the modulation 1/max(tau_n, tau_w0)
 };
 
 inline int wrap(int x, int n) {
@@ -286,7 +296,15 @@ void trace_one(const Params& P, const Table& tab, const Fields<T>& F, int is, in
         if (o.debug && (std::isnan(re(c1)) || std::isnan(re(c2)) || std::isnan(re(c3)) ||
                         std::isnan(re(c4))))
           o.err = 1;
-        tin = fmaT(w4, c4, fmaT(w3, c3, fmaT(w2, c2, w1 * c1)));
+        if (P.interp == 1) {
+          // optical-depth-modulated weights, normalised (branches on the real part)
+          auto mod = [&](const T& c) { return re(c) > P.tau_w0 ? T(1.0) / c : T(1.0 / P.tau_w0); };
+          const T v1 = w1 * mod(c1), v2 = w2 * mod(c2), v3 = w3 * mod(c3), v4 = w4 * mod(c4);
+          const T S = ((v1 + v2) + v3) + v4;
+          tin = fmaT(v4, c4, fmaT(v3, c3, fmaT(v2, c2, v1 * c1))) / S;
+        } else {
+          tin = fmaT(w4, c4, fmaT(w3, c3, fmaT(w2, c2, w1 * c1)));
+        }
       }
       const T dtp = F.dt(g);
       const T t_out = fmaT(ds, dtp, tin);
@@ -471,13 +489,20 @@ int or_shell_list(int q, int* out) {
 //                                 a private rate field, summed in chunk order
 //   debug                       : NaN-fill scratch, return 2 on an acausal read
 // Returns 0 on success, 1 on invalid arguments, 2 on a causality violation.
-int or_raytrace(int n, double cell_cm, double sigma0, double tau_lim, int kind, int E0, int E1,
-                int B, const double* gk, const double* hk, const double* nH, const double* xHI,
-                int nsrc, const int* pos, const double* ndot, const double* radius,
-                double* gamma, int cd_src, double* coldens, double* tau_in,
-                const double* wloss, double* loss, int nthreads, int debug) {
+//   interp_mode, tau_w0          : weights (or_raytrace2 only): 0 geometric, 1
+//                                 optical-depth-modulated with floor tau_w0
+int or_raytrace2(int n, double cell_cm, double sigma0, double tau_lim, int kind, int E0, int E1,
+                 int B, const double* gk, const double* hk, const double* nH, const double* xHI,
+                 int nsrc, const int* pos, const double* ndot, const double* radius,
+                 double* gamma, int cd_src, double* coldens, double* tau_in,
+                 const double* wloss, double* loss, int nthreads, int debug, int interp_mode,
+                 double tau_w0) {
   if (n < 1 || nsrc < 0) return 1;
+  if (interp_mode != 0 && interp_mode != 1) return 1;
+  if (!(tau_w0 > 0.0) || !std::isfinite(tau_w0)) return 1;
   Params P{n, cell_cm, sigma0, tau_lim};
+  P.interp = interp_mode;
+  P.tau_w0 = tau_w0;
   Table tab;
   if (!make_table(kind, E0, E1, B, gk, hk, tab)) return 1;
   const int64_t nc = (int64_t)n * n * n;
@@ -535,6 +560,16 @@ int or_raytrace(int n, double cell_cm, double sigma0, double tau_lim, int kind, 
     }
   }
   return err ? 2 : 0;
+}
+
+int or_raytrace(int n, double cell_cm, double sigma0, double tau_lim, int kind, int E0, int E1,
+                int B, const double* gk, const double* hk, const double* nH, const double* xHI,
+                int nsrc, const int* pos, const double* ndot, const double* radius,
+                double* gamma, int cd_src, double* coldens, double* tau_in,
+                const double* wloss, double* loss, int nthreads, int debug) {
+  return or_raytrace2(n, cell_cm, sigma0, tau_lim, kind, E0, E1, B, gk, hk, nH, xHI, nsrc, pos,
+                      ndot, radius, gamma, cd_src, coldens, tau_in, wloss, loss, nthreads, debug, 0,
+                      0.6);
 }
 
 // Complex-step derivatives of L = sum_p w_p Gamma_p:

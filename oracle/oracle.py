@@ -47,6 +47,12 @@ def lib():
                                     C.c_int, C.c_int, _dp, _dp]
         L.or_shell_list.restype = C.c_int
         L.or_shell_list.argtypes = [C.c_int, C.c_void_p]
+        L.or_raytrace2.restype = C.c_int
+        L.or_raytrace2.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
+                                   C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                   _dp, _dp, C.c_int, _ip, _dp, _dp,
+                                   C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double]
         L.or_raytrace.restype = C.c_int
         L.or_raytrace.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
                                   C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
@@ -136,9 +142,11 @@ def shell_list(q):
 
 def raytrace(n, cell_cm, nH, xHI, pos, ndot, radius, table: Table, sigma0=SIGMA0,
              tau_lim=TAU_LIM, gamma=True, coldens_src=-1, wloss=None, nthreads=1,
-             debug=False):
+             debug=False, interp=0, tau_w0=0.6):
     """Ray trace all sources (octahedral-shell SC).  Returns dict with
-    'gamma' (n^3 or None), 'coldens'/'tau_in' (for coldens_src), 'loss'."""
+    'gamma' (n^3 or None), 'coldens'/'tau_in' (for coldens_src), 'loss'.
+    interp: 0 the paper's geometric weights, 1 optical-depth-modulated weights
+    with floor tau_w0 (see the C file header)."""
     nH = _f64(nH).reshape(-1)
     xHI = _f64(xHI).reshape(-1)
     pos = np.ascontiguousarray(pos, dtype=np.int32).reshape(-1, 3)
@@ -154,9 +162,10 @@ def raytrace(n, cell_cm, nH, xHI, pos, ndot, radius, table: Table, sigma0=SIGMA0
     if wloss is not None:
         wloss = _f64(wloss).reshape(-1)
         loss = np.zeros(1)
-    rc = lib().or_raytrace(n, cell_cm, sigma0, tau_lim, *table.args(), nH, xHI,
-                           ndot.size, pos.reshape(-1), ndot, radius, _ptr(g), coldens_src,
-                           _ptr(cd), _ptr(ti), _ptr(wloss), _ptr(loss), nthreads, int(debug))
+    rc = lib().or_raytrace2(n, cell_cm, sigma0, tau_lim, *table.args(), nH, xHI,
+                            ndot.size, pos.reshape(-1), ndot, radius, _ptr(g), coldens_src,
+                            _ptr(cd), _ptr(ti), _ptr(wloss), _ptr(loss), nthreads, int(debug),
+                            int(interp), float(tau_w0))
     if rc == 2:
         raise RuntimeError("oracle: acausal read (an interpolant was not computed yet)")
     if rc != 0:

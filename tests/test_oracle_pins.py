@@ -309,6 +309,99 @@ def test_thin_source_cell_conserves_photons():
         assert g[c, c, c] == pytest.approx(want, rel=dt)  # 1 - O(dtau/4) from the thin value
 
 
+# ------------------ optical-depth-modulated weights (interp 1, C2Ray App. A reading)
+def _od_field(dtau, R=12.0, n=32, interp=1, tau_w0=0.6):
+    """tau_in and tau_out of one source at the centre of a box of per-cell optical depth dtau."""
+    c = n // 2
+    x = np.asarray(dtau, dtype=np.float64).reshape(-1) / (O.SIGMA0 * CELL32 * 1e-3)
+    r = O.raytrace(n, CELL32, np.full(n ** 3, 1e-3), x, [[c, c, c]], [1e50], [R],
+                   O.make_table("grey_exact"), coldens_src=0, gamma=False, debug=True,
+                   interp=interp, tau_w0=tau_w0)
+    return (r["tau_in"].reshape(n, n, n), (r["coldens"] * O.SIGMA0).reshape(n, n, n), c)
+
+
+def test_od_weights_below_the_floor_are_the_geometric_weights():
+    """Every interpolant below tau_w0: the modulation is the same constant for all four
+    and cancels in the normalisation, leaving the geometric interpolation."""
+    t0_in, t0, c = _od_field(np.full(32 ** 3, 0.02), interp=0)
+    t1_in, t1, _ = _od_field(np.full(32 ** 3, 0.02), interp=1)
+    assert t0.max() < 0.6
+    m = t0 > 0
+    assert np.array_equal(m, t1 > 0)
+    np.testing.assert_allclose(t1[m], t0[m], rtol=1e-13)
+    # the same with a floor above every tau of a thick field
+    a_in, a, _ = _od_field(np.full(32 ** 3, 3.0), interp=0)
+    b_in, b, _ = _od_field(np.full(32 ** 3, 3.0), interp=1, tau_w0=1e30)
+    np.testing.assert_allclose(b[m], a[m], rtol=1e-13)
+
+
+def test_od_weights_above_the_floor_give_the_weighted_harmonic_mean():
+    """With every interpolant above tau_w0 the modulated weights are w_n/tau_n, so
+    tau_in = sum(w_n) / sum(w_n / tau_n) = 1 / sum(w_n / tau_n): the weighted
+    harmonic mean of the interpolants' optical depths (geometric weights w_n of
+    the entry-plane interpolants, summing to 1)."""
+    n = 32
+    rng = np.random.default_rng(12)
+    dtau = 1.3 + rng.uniform(0.0, 2.0, n ** 3)  # the source cell's tau_out >= 0.65 > 0.6
+    t_in, t_out, c = _od_field(dtau, R=10.0)
+    checked = 0
+    for d in itertools.product(range(-10, 11), repeat=3):
+        m = max(abs(x) for x in d)
+        if m < 2 or sum(x * x for x in d) > 100:
+            continue
+        ad = [abs(x) for x in d]
+        ax = 2 if ad[2] == m else (1 if ad[1] == m else 0)
+        o1, o2 = [k for k in range(3) if k != ax]
+        a, b = ad[o1] / m, ad[o2] / m
+        w = [(1 - a) * (1 - b), a * (1 - b), (1 - a) * b, a * b]
+        taus = [t_out[c + e[0], c + e[1], c + e[2]] for e in _neighbours(d)]
+        want = 1.0 / sum(wn / tn for wn, tn in zip(w, taus) if wn != 0)
+        assert t_in[c + d[0], c + d[1], c + d[2]] == pytest.approx(want, rel=2e-15), d
+        checked += 1
+    assert checked > 4000
+
+
+def test_od_weights_axis_closed_form_and_symmetry():
+    t_in, t, c = _od_field(np.full(32 ** 3, 0.3), R=15.0)
+    for k in range(1, 16):
+        for v in [(0, 0, 1), (0, -1, 0), (1, 0, 0)]:
+            assert t[c + v[0] * k, c + v[1] * k, c + v[2] * k] == pytest.approx(0.3 * (k + 0.5),
+                                                                               rel=1e-14)
+    # reflections and axis permutations of a uniform medium leave the field unchanged
+    sub = t[c - 12:c + 13, c - 12:c + 13, c - 12:c + 13]
+    for perm in itertools.permutations(range(3)):
+        np.testing.assert_allclose(np.transpose(sub, perm), sub, rtol=1e-14)
+    np.testing.assert_allclose(sub[::-1, :, :], sub, rtol=1e-14)
+    np.testing.assert_allclose(sub[:, :, ::-1], sub, rtol=1e-14)
+
+
+def test_od_weights_sharpen_shadows_towards_long_characteristics():
+    """Next to an opaque block the geometric weights let the block's column leak into
+    the lit cells beside its shadow; weights favouring the less opaque interpolants
+    (the purpose of the modulation) bring those cells closer to the exact
+    long-characteristics column."""
+    n, c = 32, 16
+    x = np.full((n, n, n), 0.3 / (O.SIGMA0 * CELL32 * 1e-3))
+    x[c:c + 7, c - 6:c + 7, c + 3:c + 5] *= 1000.0  # block on the +i side of the +k axis
+    nH = np.full(n ** 3, 1e-3)
+    tab = O.make_table("grey_exact")
+    out = {}
+    for mode in (0, 1):
+        r = O.raytrace(n, CELL32, nH, x, [[c, c, c]], [1e50], [15.0], tab, coldens_src=0,
+                       gamma=False, interp=mode)
+        out[mode] = (r["coldens"] * O.SIGMA0).reshape(n, n, n)
+    lc = O.lc_tau(n, CELL32, nH, x.reshape(-1), (c, c, c), 15.0).reshape(n, n, n)
+    err = {0: [], 1: []}
+    for di in range(-6, 0):  # the lit side, beside the shadow
+        for dk in range(6, 14):
+            if di * di + dk * dk > 225:
+                continue
+            p = (c + di, c, c + dk)
+            for mode in (0, 1):
+                err[mode].append(abs(math.log(out[mode][p] / lc[p])))
+    assert np.mean(err[1]) < 0.7 * np.mean(err[0])
+
+
 # ------------------------------------------------------------ tables (Eq. tables)
 def test_grey_knots_are_exponentials():
     g, h = O.table_knots("grey")
