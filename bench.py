@@ -426,7 +426,7 @@ def main():
     # ---------------- rate-heavy variant: the same field with x_HI x 1e-4 (a nearly
     # ionised box as in the paper's Test 3), 1e5 of the sources: Gamma is non-zero over
     # most traced cells, so the rate step and the FP64 atomics run on most cells
-    rate_heavy = None
+    rate_heavy = od_weights = None
     if args.extras and rank == 0:
         k = min(100_000, len(ndot))
         rng = np.random.default_rng(13)
@@ -449,6 +449,15 @@ def main():
                       "same_sources_opaque_rate_fraction": stn["rate_cells"] / stn["source_voxels"],
                       "note": "labelled extra: Gamma accumulated with one FP64 atomicAdd per "
                               "non-zero (source, cell) term"}
+        # the same 1e5 sources with the optical-depth-modulated interpolation weights
+        g.set_interpolation("optical_depth", 0.6)
+        to = flushed_trace_ms(g, gamma, flush, "batched")
+        g.set_interpolation("geometric")
+        od_weights = {"workload": "box250 field, %d sources of the catalogue" % k,
+                      "trace_ms": to, "ns_per_source_voxel": to * 1e6 / sv_sub,
+                      "geometric_trace_ms": tn, "cost_over_geometric": to / tn,
+                      "note": "labelled extra: interpolation weights w_n / max(tau_n, 0.6), "
+                              "normalised (four reciprocals and a division per cell)"}
         g.set_sources(pos_d, ndot_d, R_d)
 
     # ---------------- adjoint: gradient throughput, 1e5 sources of the same box
@@ -615,6 +624,7 @@ def main():
             "box128_1e4src": box128,
             "ensemble64": ensemble,
             "rate_heavy": rate_heavy,
+            "od_weights": od_weights,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": w["paper_sv"] / (e2e_ms * 1e-3), "unit": UNIT,

@@ -67,6 +67,14 @@ enum {
                                bit for bit, the skipped column densities are not computed    */
 };
 
+/* Interpolation weights of Eq. interp (rt_set_interpolation). */
+enum {
+  RT_INTERP_GEOMETRIC = 0,   /* the paper's geometric (bilinear) weights, Sec. 3.1 (default) */
+  RT_INTERP_OPTICAL_DEPTH = 1 /* geometric weights modulated by 1/max(tau_n, tau_weight_min) and
+                                 normalised, after the C2Ray paper's App. A, to which Sec. 3.1
+                                 refers for the weighting: favours the less opaque interpolants */
+};
+
 /* Rate table kinds for rt_set_tables. */
 enum {
   RT_TABLE_CHORDS = 0, /* chords through knot values of g and h (Eq. tables)                */
@@ -181,6 +189,16 @@ rt_status rt_iterate(rt_grid_t g, double* d_x, double dt_s, double alpha_H, doub
  * source.  The thin/thick switch is treated as locally constant. */
 rt_status rt_raytrace_backward(rt_grid_t g, const double* d_dL_dgamma, double* d_dL_dlog_nHI,
                                double* d_dL_dlog_ndot);
+
+/* Interpolation weights of every later trace (batched and plain schedules and
+ * rt_raytrace_source_coldens): RT_INTERP_GEOMETRIC (default) or
+ * RT_INTERP_OPTICAL_DEPTH, where each interpolant's geometric weight w_n becomes
+ * w_n / max(tau_n, tau_weight_min) (tau_n its optical depth at threshold,
+ * sigma0 N_HI) and tau_in = sum(w'_n tau_n) / sum(w'_n), both sums in the order
+ * n = 1..4 of the geometric chain.  tau_weight_min finite and > 0 (0.6 is the
+ * binding's default).  The adjoint supports the geometric weights only (rt_raytrace_backward
+ * returns RT_ERR_INVALID otherwise).  RT_ERR_INVALID for other modes. */
+rt_status rt_set_interpolation(rt_grid_t g, int mode, double tau_weight_min);
 
 /* Adjoint recompute mode: with stop_at_opaque != 0 (default) each item's
  * recompute stops at its first layer whose cells all have tau_out >= 2^E1 (1+2^-40);

@@ -8,6 +8,7 @@ LIB_PATH = os.path.join(HERE, "libasora.so")
 RT_OK, RT_ERR_INVALID, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_TIMEOUT, RT_ERR_STATE, RT_ERR_BOUNDS = range(7)
 RT_SCHED_AUTO, RT_SCHED_PLAIN, RT_SCHED_BATCHED, RT_SCHED_BATCHED_EXIT = 0, 1, 2, 3
 RT_TABLE_CHORDS, RT_TABLE_GREY_EXACT = 0, 1
+RT_INTERP_GEOMETRIC, RT_INTERP_OPTICAL_DEPTH = 0, 1
 STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_OOM", 3: "RT_ERR_CUDA",
                 4: "RT_ERR_TIMEOUT", 5: "RT_ERR_STATE", 6: "RT_ERR_BOUNDS"}
 
@@ -61,6 +62,7 @@ SIGNATURES = {
     "rt_set_schedule": (_I, [_P, _I, _I, _I]),
     "rt_raytrace_backward": (_I, [_P, _P, _P, _P]),
     "rt_set_adjoint_mode": (_I, [_P, _I]),
+    "rt_set_interpolation": (_I, [_P, _I, _D]),
     "rt_autotune": (_I, [_P, C.c_char_p, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "rt_grid_destroy": (None, [_P]),
     "rt_shell_enumerate": (_I, [_I, _P]),

@@ -206,6 +206,12 @@ class Grid:
                 "rt_raytrace_backward")
         return dlogn, dlogndot[:self.nsrc]
 
+    def set_interpolation(self, mode="geometric", tau_weight_min=0.6):
+        """Interpolation weights: "geometric" (the paper's) or "optical_depth"."""
+        m = {"geometric": L.RT_INTERP_GEOMETRIC, "optical_depth": L.RT_INTERP_OPTICAL_DEPTH}[mode]
+        L.check(self._lib.rt_set_interpolation(self._h, m, float(tau_weight_min)),
+                "rt_set_interpolation")
+
     def set_adjoint_mode(self, stop_at_opaque=True):
         L.check(self._lib.rt_set_adjoint_mode(self._h, int(bool(stop_at_opaque))),
                 "rt_set_adjoint_mode")

@@ -161,6 +161,8 @@ static TraceArgs base_args(Grid& g) {
   a.itab = g.itab;
   a.itab_off = g.itab_off;
   a.neg_zero = -0.0;
+  a.interp_mode = g.interp_mode;
+  a.tau_w0 = g.tau_w0;
   a.geo_mmax = g.geo_mmax;
   a.tab.g = g.gtab;
   a.tab.h = g.htab;
@@ -764,6 +766,9 @@ rt_status rt_raytrace_backward(rt_grid_t h, const double* d_dL_dgamma, double* d
     return fail(RT_ERR_INVALID, "rt_raytrace_backward: null dL/dlog Ndot output");
   rt_status st = check_ready(g, "rt_raytrace_backward");
   if (st != RT_OK) return st;
+  if (g.interp_mode != RT_INTERP_GEOMETRIC)
+    return fail(RT_ERR_INVALID, "rt_raytrace_backward: the adjoint is built for the geometric "
+                                "weights (rt_set_interpolation mode 0)");
   TRY(launch_precompute(g));
   TRY(cudaMemsetAsync(d_dL_dlog_nHI, 0, g.ncell * sizeof(double), g.stream));
   if (g.nsrc == 0) return RT_OK;
@@ -849,6 +854,18 @@ rt_status rt_raytrace_backward(rt_grid_t h, const double* d_dL_dgamma, double* d
   g.stats.block = split > 0 ? 128 : 32;
   g.stats.grid = split > 0 ? grid_c : grid_w;
   g.stats.items = n_items;
+  return RT_OK;
+}
+
+rt_status rt_set_interpolation(rt_grid_t h, int mode, double tau_weight_min) {
+  if (!h) return fail(RT_ERR_INVALID, "rt_set_interpolation: null grid");
+  if (mode != RT_INTERP_GEOMETRIC && mode != RT_INTERP_OPTICAL_DEPTH)
+    return fail(RT_ERR_INVALID, "rt_set_interpolation: unknown mode");
+  if (!(tau_weight_min > 0.0) || !std::isfinite(tau_weight_min))
+    return fail(RT_ERR_INVALID, "rt_set_interpolation: tau_weight_min must be finite and > 0");
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  g.interp_mode = mode;
+  g.tau_w0 = tau_weight_min;
   return RT_OK;
 }
 

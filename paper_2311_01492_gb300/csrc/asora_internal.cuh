@@ -93,6 +93,8 @@ struct TraceArgs {
   unsigned long long* rate_cells;  // number of rate evaluations (may be null)
   int early_exit;        // stop an item once a whole layer is opaque (rates only)
   double neg_zero;       // -0.0 at run time: fma(x, y, -0.0) is x*y bit for bit, as a DFMA
+  int interp_mode;       // 0: geometric weights (Eq. interp); 1: optical-depth-modulated
+  double tau_w0;         // floor of the modulation 1/max(tau_n, tau_w0) (mode 1)
   uint64_t exit_bits;    // bits of the opacity bound 2^E1 (1 + 2^-40)
   // Row tables of unclipped quadrant layers, one blob per (R^2 limit, m):
   // first flat index of rows 0..H+1 (ints) then the row of every flat index
@@ -216,6 +218,8 @@ struct Grid {
   double* dq_merged = nullptr;   // adjoint: dL/dlog Ndot per merged source
   int dq_cap = 0;
   int bwd_exit = 1;              // adjoint: stop each item's recompute at its first opaque layer
+  int interp_mode = 0;           // interpolation weights (rt_set_interpolation)
+  double tau_w0 = 0.6;
   bool capturing = false;
 
   // stats

@@ -50,6 +50,22 @@ __device__ __forceinline__ double cell_rate(const TraceArgs& a, double nd, doubl
   return nd * (dg * invv_cell * invn);
 }
 
+// Interpolated column (Eq. interp) with optical-depth-modulated weights
+// (interpolation mode 1, after the C2Ray paper's App. A, to which Sec. 3.1
+// refers for the weighting): each geometric weight times 1/max(c_n, tw0), the
+// sum normalised by the modulated weights, summed in the same order as the
+// geometric chain.
+__device__ __forceinline__ double od_interp(double w1, double w2, double w3, double w4, double c1,
+                                            double c2, double c3, double c4, double tw0,
+                                            double nz) {
+  const double v1 = w1 * (1.0 / fmax(c1, tw0));
+  const double v2 = w2 * (1.0 / fmax(c2, tw0));
+  const double v3 = w3 * (1.0 / fmax(c3, tw0));
+  const double v4 = w4 * (1.0 / fmax(c4, tw0));
+  const double S = ((v1 + v2) + v3) + v4;
+  return fma(v4, c4, fma(v3, c3, fma(v2, c2, fma(v1, c1, nz)))) / S;
+}
+
 // Slope of the table at tau (derivative of the lookup): the chord slope c1
 // of tau's segment, 0 at and beyond the table's upper bound; -exp(-tau) for
 // exact grey opacity.

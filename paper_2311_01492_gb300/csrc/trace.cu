@@ -65,7 +65,7 @@ size_t faces_smem_bytes(int hcap, int block) {
 // Row tables: for an item whose window does not clip any layer, the tables of
 // layer m+1 are copied (cp.async) from the precomputed blobs of its R^2 limit
 // while layer m is traced; otherwise warp 0 builds them during layer m.
-template <int GS, bool COLDENS>
+template <int GS, bool COLDENS, bool OD>
 __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int item, const int gt,
                                                 unsigned char* __restrict__ sm, const int h,
                                                 unsigned& nrate) {
@@ -198,7 +198,10 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
         // w1*v1 as fma(w1, v1, -0.0): the same value for every input (the sum of the
         // exact product and -0 rounds like the product alone, and +0 + -0 = +0), on
         // GB300 issued as a DFMA, which retires at least as fast as a DMUL
-        tin = fma(w4, v4, fma(w3, v3, fma(w2, v2, fma(w1, v1, a.neg_zero))));
+        if (OD)
+          tin = od_interp(w1, w2, w3, w4, v1, v2, v3, v4, a.tau_w0, a.neg_zero);
+        else
+          tin = fma(w4, v4, fma(w3, v3, fma(w2, v2, fma(w1, v1, a.neg_zero))));
       }
       const double tout = fma(dtp, ds, tin);
       if (GS == 32) {
@@ -260,12 +263,12 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
 
 // The four quadrants of a clipped face one after another, kept out of line so
 // that it does not weigh on the registers of the whole-face loop.
-template <int GS, bool COLDENS>
+template <int GS, bool COLDENS, bool OD>
 __device__ __noinline__ void trace_face_by_quadrants(const TraceArgs& a, const int item,
                                                      const int gt, unsigned char* sm, const int h,
                                                      unsigned& nrate) {
   for (int k = 0; k < 4; ++k) {
-    trace_face_item<GS, COLDENS>(a, (item & ~3) | k, gt, sm, h, nrate);
+    trace_face_item<GS, COLDENS, OD>(a, (item & ~3) | k, gt, sm, h, nrate);
     group_sync<GS>();
   }
 }
@@ -328,7 +331,7 @@ __device__ __forceinline__ void face_cell(const int j, const int m, const int nE
 // weights per cell and take the two-term form, which rounds exactly like the
 // full chain (the zero terms add exactly +0).  Faces whose layers the window
 // clips are traced quadrant by quadrant (trace_face_item) instead.
-template <int GS, bool COLDENS>
+template <int GS, bool COLDENS, bool OD>
 __device__ __forceinline__ void trace_face_whole(const TraceArgs& a, const int item, const int gt,
                                                  unsigned char* __restrict__ sm, const int h,
                                                  unsigned& nrate) {
@@ -344,7 +347,7 @@ __device__ __forceinline__ void trace_face_whole(const TraceArgs& a, const int i
     if (sl >= 0 && a.rtab_hcap[sl] <= min(B.whi, -B.wlo)) toff = a.itab_off + a.rtab_first[sl] - 1;
   }
   if (!toff) {
-    trace_face_by_quadrants<GS, COLDENS>(a, item & ~3, gt, sm, h, nrate);
+    trace_face_by_quadrants<GS, COLDENS, OD>(a, item & ~3, gt, sm, h, nrate);
     return;
   }
   const int N = B.n;
@@ -442,6 +445,9 @@ __device__ __forceinline__ void trace_face_whole(const TraceArgs& a, const int i
       double tin;
       if (m == 1) {
         tin = half_dts * ds;
+      } else if (OD) {
+        tin = od_interp(wv0.x, wv0.y, wv1.x, wv1.y, ctr[o1], ctr[o2], ctr[o3], ctr[o4], a.tau_w0,
+                        a.neg_zero);
       } else if (__all_sync(0xffffffffu, cls != CLS_I)) {
         // rim row (w1 = w3 = 0), rim column (w1 = w2 = 0), axis t1 = 0 (w2 = w4 = 0),
         // axis t2 = 0 (w3 = w4 = 0)
@@ -508,7 +514,7 @@ __device__ __forceinline__ void flush_rate_count(const TraceArgs& a, unsigned nr
 // 128-thread CTAs per SM (56 registers; the shared memory of nine fits) measured
 // faster than eight at 64 or fewer at 72-80 registers: latency, not registers,
 // limits this loop.
-template <int BLOCK, bool COLDENS>
+template <int BLOCK, bool COLDENS, bool OD>
 __global__ void __launch_bounds__(BLOCK, 1152 / BLOCK) k_trace_faces(TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
@@ -523,7 +529,7 @@ __global__ void __launch_bounds__(BLOCK, 1152 / BLOCK) k_trace_faces(TraceArgs a
     __syncthreads();
     const int it = s_item;
     if (it >= a.n_items) break;
-    trace_face_item<BLOCK, COLDENS>(a, a.items[it], threadIdx.x, smem_raw, a.hcap, nrate);
+    trace_face_item<BLOCK, COLDENS, OD>(a, a.items[it], threadIdx.x, smem_raw, a.hcap, nrate);
   }
   flush_rate_count(a, nrate);
 }
@@ -532,7 +538,7 @@ __global__ void __launch_bounds__(BLOCK, 1152 / BLOCK) k_trace_faces(TraceArgs a
 // slice of shared memory and warp-level synchronisation only.
 // The CTA holds 1..8 warps (blockDim.x / 32), chosen at launch so that the most
 // warps stay resident for the shared memory one warp needs.
-template <bool COLDENS>
+template <bool COLDENS, bool OD>
 __global__ void __launch_bounds__(256, 4) k_trace_faces_warp(TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (a.skip && *a.skip) return;
@@ -548,7 +554,7 @@ __global__ void __launch_bounds__(256, 4) k_trace_faces_warp(TraceArgs a) {
     if (lane == 0) it = a.item_begin + atomicAdd(a.queue, 1);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= a.n_items) break;
-    trace_face_item<32, COLDENS>(a, a.items[it], lane, my, a.hcap, nrate);
+    trace_face_item<32, COLDENS, OD>(a, a.items[it], lane, my, a.hcap, nrate);
     __syncwarp();
   }
   flush_rate_count(a, nrate);
@@ -558,7 +564,7 @@ __global__ void __launch_bounds__(256, 4) k_trace_faces_warp(TraceArgs a) {
 // items are faces, face it being the quadrant-0 item items[4 it].  Up to 80
 // registers (measured faster than 64, where the loop spills); shared memory
 // bounds the warps per SM for these faces anyway.
-template <bool COLDENS>
+template <bool COLDENS, bool OD>
 __global__ void __launch_bounds__(256, 3) k_trace_faces_whole_warp(TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (a.skip && *a.skip) return;
@@ -574,7 +580,7 @@ __global__ void __launch_bounds__(256, 3) k_trace_faces_whole_warp(TraceArgs a) 
     if (lane == 0) it = a.item_begin + atomicAdd(a.queue, 1);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= a.n_items) break;
-    trace_face_whole<32, COLDENS>(a, a.items[4 * it], lane, my, a.hcap, nrate);
+    trace_face_whole<32, COLDENS, OD>(a, a.items[4 * it], lane, my, a.hcap, nrate);
     __syncwarp();
   }
   flush_rate_count(a, nrate);
@@ -583,27 +589,35 @@ __global__ void __launch_bounds__(256, 3) k_trace_faces_whole_warp(TraceArgs a) 
 // Kernel variant for (block, warps per CTA, coldens): block 128/256 = CTA mode,
 // 32 = warp mode and 4 = whole-face warp mode with wpb warps per CTA (1..8).  Null
 // if not instantiated.
-static const void* face_kernel(int block, int wpb, bool coldens) {
+static const void* face_kernel(int block, int wpb, bool coldens, bool od) {
+#define ASORA_PICK(K) (od ? (coldens ? (const void*)K<true, true> : (const void*)K<false, true>) \
+                          : (coldens ? (const void*)K<true, false> : (const void*)K<false, false>))
   switch (block) {
     case 32:
       if (wpb < 1 || wpb > 8) return nullptr;
-      return coldens ? (const void*)k_trace_faces_warp<true> : (const void*)k_trace_faces_warp<false>;
+      return ASORA_PICK(k_trace_faces_warp);
     case 4:  // whole-face warp mode, wpb warps per CTA
       if (wpb < 1 || wpb > 8) return nullptr;
-      return coldens ? (const void*)k_trace_faces_whole_warp<true>
-                     : (const void*)k_trace_faces_whole_warp<false>;
-    case 128: return coldens ? (const void*)k_trace_faces<128, true>
-                             : (const void*)k_trace_faces<128, false>;
-    case 256: return coldens ? (const void*)k_trace_faces<256, true>
-                             : (const void*)k_trace_faces<256, false>;
+      return ASORA_PICK(k_trace_faces_whole_warp);
+    case 128:
+      return od ? (coldens ? (const void*)k_trace_faces<128, true, true>
+                           : (const void*)k_trace_faces<128, false, true>)
+                : (coldens ? (const void*)k_trace_faces<128, true, false>
+                           : (const void*)k_trace_faces<128, false, false>);
+    case 256:
+      return od ? (coldens ? (const void*)k_trace_faces<256, true, true>
+                           : (const void*)k_trace_faces<256, false, true>)
+                : (coldens ? (const void*)k_trace_faces<256, true, false>
+                           : (const void*)k_trace_faces<256, false, false>);
     default: return nullptr;
   }
+#undef ASORA_PICK
 }
 
 cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid, size_t smem,
                                int wpb) {
   const bool cd = a.coldens != nullptr;
-  const void* fn = face_kernel(block, wpb, cd);
+  const void* fn = face_kernel(block, wpb, cd, a.interp_mode == RT_INTERP_OPTICAL_DEPTH);
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -619,7 +633,7 @@ int faces_max_grid(int block, size_t smem, int wpb) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const void* fn = face_kernel(block, wpb, false);
+  const void* fn = face_kernel(block, wpb, false, false);
   if (!fn) return 0;
   const int threads = (block == 32 || block == 4) ? wpb * 32 : block;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -655,7 +669,7 @@ __host__ __device__ inline void shell_cell(int q, int t, int& di, int& dj, int& 
   dk = up ? h : -h;
 }
 
-template <int BLOCK>
+template <int BLOCK, bool OD>
 __global__ void __launch_bounds__(BLOCK) k_trace_shells(TraceArgs a) {
   __shared__ int s_item;
   const int E = a.hcap;
@@ -751,7 +765,10 @@ __global__ void __launch_bounds__(BLOCK) k_trace_shells(TraceArgs a) {
           const double c2 = cube[cidx(e2[0], e2[1], e2[2])];
           const double c3 = cube[cidx(e3[0], e3[1], e3[2])];
           const double c4 = cube[cidx(e4[0], e4[1], e4[2])];
-          tin = fma(w4, c4, fma(w3, c3, fma(w2, c2, w1 * c1)));
+          if (OD)
+            tin = od_interp(w1, w2, w3, w4, c1, c2, c3, c4, a.tau_w0, a.neg_zero);
+          else
+            tin = fma(w4, c4, fma(w3, c3, fma(w2, c2, w1 * c1)));
         }
         const double dtp = __ldg(&a.dtau[cell]);
         const double tout = fma(dtp, ds, tin);
@@ -773,10 +790,20 @@ __global__ void __launch_bounds__(BLOCK) k_trace_shells(TraceArgs a) {
 }
 
 cudaError_t launch_trace_shells(Grid& g, const TraceArgs& a, int block, int grid) {
+  const bool od = a.interp_mode == RT_INTERP_OPTICAL_DEPTH;
   switch (block) {
-    case 128: k_trace_shells<128><<<grid, 128, 0, g.stream>>>(a); break;
-    case 256: k_trace_shells<256><<<grid, 256, 0, g.stream>>>(a); break;
-    case 512: k_trace_shells<512><<<grid, 512, 0, g.stream>>>(a); break;
+    case 128:
+      if (od) k_trace_shells<128, true><<<grid, 128, 0, g.stream>>>(a);
+      else k_trace_shells<128, false><<<grid, 128, 0, g.stream>>>(a);
+      break;
+    case 256:
+      if (od) k_trace_shells<256, true><<<grid, 256, 0, g.stream>>>(a);
+      else k_trace_shells<256, false><<<grid, 256, 0, g.stream>>>(a);
+      break;
+    case 512:
+      if (od) k_trace_shells<512, true><<<grid, 512, 0, g.stream>>>(a);
+      else k_trace_shells<512, false><<<grid, 512, 0, g.stream>>>(a);
+      break;
     default: return cudaErrorInvalidValue;
   }
   count_launch();
@@ -788,9 +815,9 @@ int shells_max_grid(int block) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e = cudaErrorInvalidValue;
-  if (block == 128) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace_shells<128>, 128, 0);
-  if (block == 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace_shells<256>, 256, 0);
-  if (block == 512) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace_shells<512>, 512, 0);
+  if (block == 128) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace_shells<128, false>, 128, 0);
+  if (block == 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace_shells<256, false>, 256, 0);
+  if (block == 512) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace_shells<512, false>, 512, 0);
   if (e != cudaSuccess) return 0;
   return per * sms;
 }

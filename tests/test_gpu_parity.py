@@ -67,11 +67,14 @@ def assert_gamma(gg, go, rtol=GAMMA_RTOL):
         assert rel.max() <= rtol, "max rel err %.3e" % rel.max()
 
 
-def run_both(w, tab, schedules=("batched", "plain", "early_exit"), cd_srcs=(0,), sched=None):
+def run_both(w, tab, schedules=("batched", "plain", "early_exit"), cd_srcs=(0,), sched=None,
+             interp=0, tau_w0=0.6):
     n, cell = w["n"], w["cell_cm"]
     ref = O.raytrace(n, cell, w["nH"], w["xHI"], w["pos"], w["ndot"], w["radius"], tab,
-                     nthreads=8)
+                     nthreads=8, interp=interp, tau_w0=tau_w0)
     g = make_gpu(n, cell, w["nH"], w["xHI"], w["pos"], w["ndot"], w["radius"], tab)
+    if interp:
+        g.set_interpolation("optical_depth", tau_w0)
     if sched is not None:
         g.set_schedule(*sched)
     for sch in schedules:
@@ -84,7 +87,8 @@ def run_both(w, tab, schedules=("batched", "plain", "early_exit"), cd_srcs=(0,),
         for s in cd_srcs:
             cd = g.source_coldens(s, schedule=sch).cpu().numpy()
             ro = O.raytrace(n, cell, w["nH"], w["xHI"], w["pos"][s:s + 1], w["ndot"][s:s + 1],
-                            w["radius"][s:s + 1], tab, gamma=False, coldens_src=0)
+                            w["radius"][s:s + 1], tab, gamma=False, coldens_src=0,
+                            interp=interp, tau_w0=tau_w0)
             if not np.array_equal(cd, ro["coldens"]):
                 bad = np.flatnonzero(cd != ro["coldens"])
                 raise AssertionError(
@@ -152,6 +156,40 @@ def test_every_batched_configuration(sched):
                  xHI=np.full((n, n, n), 1e-4), pos=np.zeros((1, 3), np.int32),
                  ndot=np.array([1e50]), radius=np.array([R]))
         run_both(w, table("bb"), schedules=("batched",), sched=sched)
+
+
+@pytest.mark.parametrize("sched", [(128, 0, 0), (256, 11, 0), (128, 24, 13), (128, 32, 20)])
+def test_optical_depth_weights_match_oracle(sched):
+    """Optical-depth-modulated weights (interpolation mode 1): the same column densities
+    as the oracle's mode 1, bit for bit, and rates to 1e-9, in every schedule and launch
+    configuration, with clipped windows, thin and thick cells and several floors."""
+    for n, nsrc, rmax, seed in [(16, 20, 12.0, 1), (17, 30, 25.0, 2), (24, 40, 12.0, 3),
+                                (9, 5, 40.0, 4)]:
+        w = _random_box(n, nsrc, rmax, seed)
+        for tw0 in (0.6, 1e-3):
+            run_both(w, table("bb"), cd_srcs=(0, 1, 3), sched=sched, interp=1, tau_w0=tw0)
+    # a partly ionised field, so that interpolants fall on both sides of the floor (chord
+    # tables: with exact exp(-tau), CUDA's and libm's last-ulp differences are amplified
+    # ~1/dtau in g(tau_in) - g(tau_out) when dtau*ds is just above the thin switch)
+    w = _random_box(24, 12, 12.0, 5)
+    w["xHI"] = w["xHI"] * 3e-4
+    run_both(w, table("bb"), cd_srcs=(0, 2), sched=sched, interp=1, tau_w0=0.6)
+
+
+def test_optical_depth_weights_rejected_by_the_adjoint_and_checked():
+    api = A()
+    w = _random_box(16, 4, 6.0, 6)
+    g = make_gpu(w["n"], w["cell_cm"], w["nH"], w["xHI"], w["pos"], w["ndot"], w["radius"],
+                 table("bb"))
+    from paper_2311_01492_gb300 import _lib as L
+    for bad in [(2, 0.6), (-1, 0.6), (1, 0.0), (1, -1.0), (1, float("inf")), (1, float("nan"))]:
+        assert g._lib.rt_set_interpolation(g._h, *bad) == L.RT_ERR_INVALID
+    g.set_interpolation("optical_depth", 0.6)
+    with pytest.raises(api.RtError, match="RT_ERR_INVALID"):
+        g.backward(dev(np.ones(16 ** 3)))
+    g.set_interpolation("geometric")
+    g.backward(dev(np.ones(16 ** 3)))
+    g.close()
 
 
 def test_precomputed_row_tables_are_built_for_unclipped_radii():
