@@ -409,19 +409,25 @@ def main():
                           "fully opaque layer (exact for the rates)"}
     K_IT = 3
     xw = x0_d.clone()
-    flush.fill_(7.0)
-    torch.cuda.synchronize()
-    i0 = torch.cuda.Event(enable_timing=True)
-    i1 = torch.cuda.Event(enable_timing=True)
-    i0.record(stream)
-    g.iterate(xw, dt, max_iter=K_IT, conv_frac=0.0, use_graph=True)
-    i1.record(stream)
-    torch.cuda.synchronize()
-    it_ms = i0.elapsed_time(i1)
+    gw = torch.empty_like(gamma)
+    it_ms = []
+    for rep in range(2):  # first call captures the graph, the second replays it
+        xw.copy_(x0_d)
+        flush.fill_(7.0 + rep)
+        torch.cuda.synchronize()
+        i0 = torch.cuda.Event(enable_timing=True)
+        i1 = torch.cuda.Event(enable_timing=True)
+        i0.record(stream)
+        g.iterate(xw, dt, max_iter=K_IT, conv_frac=0.0, use_graph=True, gamma=gw)
+        i1.record(stream)
+        torch.cuda.synchronize()
+        it_ms.append(i0.elapsed_time(i1))
     g.set_xHI(xHI_d)  # the iteration leaves the grid on its own x_HI; restore the workload's
-    iterate = {"iterations": K_IT, "ms_total": it_ms, "ms_per_iteration": it_ms / K_IT,
-               "note": "graph capture and instantiation included; each iteration = dtau "
-                       "precompute + batched trace + chemistry + convergence count"}
+    iterate = {"iterations": K_IT, "ms_total_first_call": it_ms[0],
+               "ms_total_replay": it_ms[1], "ms_per_iteration": it_ms[1] / K_IT,
+               "note": "one CUDA graph of K iterations, captured on the first call and "
+                       "replayed by the second; each iteration = dtau precompute + batched "
+                       "trace + chemistry + convergence count"}
 
     # ---------------- rate-heavy variant: the same field with x_HI x 1e-4 (a nearly
     # ionised box as in the paper's Test 3), 1e5 of the sources: Gamma is non-zero over

@@ -171,7 +171,10 @@ rt_status rt_chemistry_step(rt_grid_t g, const double* d_gamma, const double* d_
  * {x_HI = 1-<x>; Gamma = trace; <x> = chemistry} until fewer than
  * conv_frac * ncells cells are unconverged or max_iter iterations.  With
  * use_graph != 0 the max_iter iterations are one captured CUDA graph whose
- * later iterations are no-ops once converged.  d_gamma receives the last
+ * later iterations are no-ops once converged; the graph is kept and replayed by
+ * later calls with the same d_x, d_gamma, dt_s, alpha_H, C_H, max_iter,
+ * conv_tol, conv_frac and stream when no rt_set_*, rt_autotune or
+ * rt_set_schedule call came in between (otherwise it is captured again).  d_gamma receives the last
  * rates; *h_iters (host, may be NULL) the iterations run (synchronises).
  * Requires rt_set_density; the grid's registered x_HI is replaced by an
  * internal buffer. */

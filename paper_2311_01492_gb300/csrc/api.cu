@@ -93,6 +93,8 @@ static void free_grid(Grid* g) {
   dev_free(g->xavg2); dev_free(g->xhi_int); dev_free(g->flags); dev_free(g->counters);
   dev_free(g->bwd_stack); dev_free(g->dq_merged);
   free_row_tables(*g);
+  if (g->it_exec) cudaGraphExecDestroy(g->it_exec);
+  if (g->it_stream) cudaStreamDestroy(g->it_stream);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
   delete g;
@@ -423,7 +425,9 @@ rt_status rt_grid_create(rt_grid_t* out, int n, double cell_cm, const rt_params*
 
 rt_status rt_set_stream(rt_grid_t h, rt_stream_t s) {
   if (!h) return fail(RT_ERR_INVALID, "rt_set_stream: null grid");
-  reinterpret_cast<Grid*>(h)->stream = (cudaStream_t)s;
+  Grid& g = *reinterpret_cast<Grid*>(h);
+  g.stream = (cudaStream_t)s;
+  ++g.epoch;
   return RT_OK;
 }
 
@@ -476,6 +480,7 @@ rt_status rt_set_tables(rt_grid_t h, int kind, int E0, int E1, int bits, const d
   g.E1 = E1;
   g.B = bits;
   g.have_tables = true;
+  ++g.epoch;
   return RT_OK;
 }
 
@@ -493,6 +498,7 @@ static rt_status set_field(rt_grid_t h, const double* d, bool density) {
     return fail(RT_ERR_INVALID, density ? "rt_set_density: n_H must be finite, >= +0 and <= 1e12"
                                         : "rt_set_xHI: x_HI must lie in [+0, 1]");
   if (density) g.nH = d; else g.xHI = d;
+  ++g.epoch;
   return RT_OK;
 }
 
@@ -507,6 +513,7 @@ rt_status rt_set_scale_factor(rt_grid_t h, double a) {
   TRY(cudaMemcpyAsync(g.boxes_d, g.boxes_h.data(), g.nbox * sizeof(BoxDev), cudaMemcpyHostToDevice,
                       g.stream));
   TRY(cudaStreamSynchronize(g.stream));  // the host records may change again
+  ++g.epoch;
   return RT_OK;
 }
 
@@ -520,6 +527,7 @@ rt_status rt_set_sources(rt_grid_t h, int nsrc, const int32_t* d_pos, const int3
   if (nsrc > 0 && (!d_pos || !d_ndot || !d_radius))
     return fail(RT_ERR_INVALID, "rt_set_sources: null source array");
   Grid& g = *reinterpret_cast<Grid*>(h);
+  ++g.epoch;  // the source arrays, tables and geometry may move
   rt_status st = ingest_sources(g, nsrc, d_pos, d_box, d_ndot, d_radius);
   if (st == RT_OK) {
     const int mmax = std::max(1, std::min(isqrt_h(g.max_r2), g.nmax / 2 + 1));
@@ -682,7 +690,6 @@ rt_status rt_iterate(rt_grid_t h, double* d_x, double dt_s, double alpha_H, doub
   g.xHI = g.xhi_int;
   const int64_t limit = (int64_t)std::ceil(conv_frac * (double)g.ncell);
   cudaStream_t user = g.stream;
-  cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   rt_status st = RT_OK;
@@ -707,33 +714,48 @@ rt_status rt_iterate(rt_grid_t h, double* d_x, double dt_s, double alpha_H, doub
   TRY(cudaMemcpyAsync(g.xavg, d_x, bytes, cudaMemcpyDeviceToDevice, user));
   TRY(cudaMemsetAsync(g.flags, 0, 2 * sizeof(int), user));
   if (use_graph) {
-    // capture on a private stream ordered after the user's stream
-    TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    TRY(cudaEventRecord(g.ev[3], user));
-    TRY(cudaStreamWaitEvent(cap, g.ev[3], 0));
-    g.stream = cap;
-    g.capturing = true;
-    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      for (int k = 0; k < max_iter && st == RT_OK; ++k) st = body(k);
-      cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
-      if (st == RT_OK && e2 != cudaSuccess) st = cuda_fail(e2, "cudaStreamEndCapture");
-    } else {
-      st = cuda_fail(e, "cudaStreamBeginCapture");
+    // capture once on a private stream; replay while the arguments and the grid's
+    // state are those it was captured with
+    const Grid::IterKey key{d_x, d_gamma, dt_s, alpha_H, C_H, conv_tol, conv_frac, max_iter,
+                            g.epoch, user};
+    if (!g.it_stream) TRY(cudaStreamCreateWithFlags(&g.it_stream, cudaStreamNonBlocking));
+    cudaStream_t cap = g.it_stream;
+    if (!g.it_exec || !(key == g.it_key)) {
+      if (g.it_exec) {
+        TRY(cudaStreamSynchronize(cap));  // the old graph may still run
+        cudaGraphExecDestroy(g.it_exec);
+        g.it_exec = nullptr;
+      }
+      g.stream = cap;
+      g.capturing = true;
+      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        for (int k = 0; k < max_iter && st == RT_OK; ++k) st = body(k);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (st == RT_OK && e2 != cudaSuccess) st = cuda_fail(e2, "cudaStreamEndCapture");
+      } else {
+        st = cuda_fail(e, "cudaStreamBeginCapture");
+      }
+      g.capturing = false;
+      g.stream = user;
+      if (st == RT_OK) {
+        cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+        if (e3 != cudaSuccess) st = cuda_fail(e3, "cudaGraphInstantiate");
+      }
+      if (graph) cudaGraphDestroy(graph);
+      if (st != RT_OK) {
+        if (exec) cudaGraphExecDestroy(exec);
+        return st;
+      }
+      g.it_exec = exec;
+      g.it_key = key;
     }
-    g.capturing = false;
-    g.stream = user;
-    if (st == RT_OK) {
-      cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
-      if (e3 == cudaSuccess) e3 = cudaGraphLaunch(exec, cap);
-      if (e3 == cudaSuccess) e3 = cudaEventRecord(g.ev[3], cap);
-      if (e3 == cudaSuccess) e3 = cudaStreamWaitEvent(user, g.ev[3], 0);
-      if (e3 != cudaSuccess) st = cuda_fail(e3, "graph launch");
-    }
-    if (exec) cudaGraphExecDestroy(exec);  // deferred until the launch completes
-    if (graph) cudaGraphDestroy(graph);
-    if (cap) cudaStreamDestroy(cap);
-    if (st != RT_OK) return st;
+    cudaError_t e4 = cudaEventRecord(g.ev[3], user);
+    if (e4 == cudaSuccess) e4 = cudaStreamWaitEvent(cap, g.ev[3], 0);
+    if (e4 == cudaSuccess) e4 = cudaGraphLaunch(g.it_exec, cap);
+    if (e4 == cudaSuccess) e4 = cudaEventRecord(g.ev[3], cap);
+    if (e4 == cudaSuccess) e4 = cudaStreamWaitEvent(user, g.ev[3], 0);
+    if (e4 != cudaSuccess) return cuda_fail(e4, "graph launch");
   } else {
     for (int k = 0; k < max_iter; ++k) {
       st = body(k);
@@ -866,6 +888,7 @@ rt_status rt_set_interpolation(rt_grid_t h, int mode, double tau_weight_min) {
   Grid& g = *reinterpret_cast<Grid*>(h);
   g.interp_mode = mode;
   g.tau_w0 = tau_weight_min;
+  ++g.epoch;
   return RT_OK;
 }
 
@@ -887,6 +910,7 @@ rt_status rt_set_schedule(rt_grid_t h, int block_big, int hsmall, int hface) {
   g.block_big = block_big;
   g.hsmall = hsmall;
   g.hface = hface;
+  ++g.epoch;
   return RT_OK;
 }
 
@@ -905,6 +929,7 @@ rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_
                       int* h_hface) {
   if (!h) return fail(RT_ERR_INVALID, "rt_autotune: null grid");
   Grid& g = *reinterpret_cast<Grid*>(h);
+  ++g.epoch;  // the schedule may change
   rt_status st = check_ready(g, "rt_autotune");
   if (st != RT_OK) return st;
   auto report = [&]() {

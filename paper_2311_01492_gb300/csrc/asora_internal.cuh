@@ -221,6 +221,25 @@ struct Grid {
   int interp_mode = 0;           // interpolation weights (rt_set_interpolation)
   double tau_w0 = 0.6;
   bool capturing = false;
+  // rt_iterate's CUDA graph, kept for the next call with the same arguments and
+  // no state change in between (epoch: bumped by every call that changes a
+  // pointer, a launch configuration or a value a captured kernel uses)
+  uint64_t epoch = 0;
+  cudaGraphExec_t it_exec = nullptr;
+  cudaStream_t it_stream = nullptr;
+  struct IterKey {
+    double* x = nullptr;
+    double* gamma = nullptr;
+    double dt = 0, alpha = 0, C = 0, conv_tol = 0, conv_frac = 0;
+    int max_iter = 0;
+    uint64_t epoch = 0;
+    cudaStream_t user = nullptr;
+    bool operator==(const IterKey& o) const {
+      return x == o.x && gamma == o.gamma && dt == o.dt && alpha == o.alpha && C == o.C &&
+             conv_tol == o.conv_tol && conv_frac == o.conv_frac && max_iter == o.max_iter &&
+             epoch == o.epoch && user == o.user;
+    }
+  } it_key;
 
   // stats
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};

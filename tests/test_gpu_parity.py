@@ -400,3 +400,49 @@ def test_iterate_matches_oracle_fixed_iterations(use_graph):
     gam2, it2 = g.iterate(xd2, dt, max_iter=5, conv_frac=1.0, use_graph=use_graph)
     assert it2 == 1
     g.close()
+
+
+def test_iterate_graph_is_kept_and_replayed():
+    """rt_iterate captures its CUDA graph once: a second call with the same arguments
+    replays it (no kernel launched from the host) with the same result as the first and
+    as the uncaptured loop; a state change (new sources) makes the next call capture
+    again; a different argument (dt) too."""
+    from paper_2311_01492_gb300 import _lib as L
+    n = 16
+    cell = 10 * S.KPC_CM / n
+    nH = np.full(n ** 3, 1e-3)
+    x = np.zeros(n ** 3)
+    src = np.array([[8, 8, 8], [3, 12, 5]], np.int32)
+    ndot, R = np.array([1e48, 3e47]), np.array([7.5, 5.0])
+    tab = table("grey_exact")
+    dt = 50 * S.MYR_S
+    g = make_gpu(n, cell, nH, 1.0 - x, src, ndot, R, tab)
+    lib = L.lib()
+    xa = dev(x)
+    gam = dev(np.zeros(n ** 3))
+    g.iterate(xa, dt, max_iter=3, conv_frac=0.0, use_graph=True, gamma=gam)
+    first = (xa.cpu().numpy(), gam.cpu().numpy())
+    n0 = lib.rt_kernel_launch_count()
+    xb = dev(x)
+    xa.copy_(xb)  # same pointers as the first call, same start
+    g.iterate(xa, dt, max_iter=3, conv_frac=0.0, use_graph=True, gamma=gam)
+    assert lib.rt_kernel_launch_count() == n0  # replayed, nothing captured
+    assert np.array_equal(xa.cpu().numpy(), first[0])
+    assert np.array_equal(gam.cpu().numpy(), first[1])
+    xc = dev(x)
+    gc, _ = g.iterate(xc, dt, max_iter=3, conv_frac=0.0, use_graph=False)
+    np.testing.assert_allclose(xc.cpu().numpy(), first[0], rtol=1e-14, atol=1e-300)
+    # new sources: captured again, and the rates follow the new catalogue
+    g.set_sources(dev(src[:1], torch.int32), dev(ndot[:1]), dev(R[:1]))
+    xa.copy_(xb)
+    n1 = lib.rt_kernel_launch_count()
+    g.iterate(xa, dt, max_iter=3, conv_frac=0.0, use_graph=True, gamma=gam)
+    assert lib.rt_kernel_launch_count() > n1
+    xo, Go = _oracle_step(n, cell, nH, x, src[:1], ndot[:1], R[:1], tab, dt, 3)
+    np.testing.assert_allclose(xa.cpu().numpy(), xo, rtol=1e-9, atol=1e-300)
+    # another dt: captured again
+    n2 = lib.rt_kernel_launch_count()
+    xa.copy_(xb)
+    g.iterate(xa, 2 * dt, max_iter=3, conv_frac=0.0, use_graph=True, gamma=gam)
+    assert lib.rt_kernel_launch_count() > n2
+    g.close()
