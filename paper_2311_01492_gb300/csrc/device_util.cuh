@@ -40,14 +40,16 @@ __device__ __forceinline__ double tab_eval(const double2* __restrict__ t, const 
 }
 
 // Rate of one cell (photon-conserving, Eq. sugg; thin limit Eq. gammalocal).
-__device__ __forceinline__ double cell_rate(const TraceArgs& a, double nd, double tin, double tout,
-                                            double dcell, double invv_cell, double thin_cell,
-                                            double invn) {
-  if (bits_of(dcell) <= bits_of(a.tau_lim)) {
-    return nd * (tab_eval(a.tab.h, a.tab, tin) * thin_cell);
-  }
+// nd_thick = Ndot / alpha^3 and nd_thin = Ndot sigma0 / alpha^2 are per source
+// and box; the geometry entry holds 1/(4 pi r^2 ds) and 1/(4 pi r^2) in cell units.
+// Only the branch taken reads its geometry and 1/n_HI.
+__device__ __forceinline__ double cell_rate(const TraceArgs& a, double nd_thick, double nd_thin,
+                                            double tin, double tout, double dcell,
+                                            const GeoEntry* ge, const double* invn) {
+  if (bits_of(dcell) <= bits_of(a.tau_lim))
+    return nd_thin * (tab_eval(a.tab.h, a.tab, tin) * __ldg(&ge->thin));
   const double dg = tab_eval(a.tab.g, a.tab, tin) - tab_eval(a.tab.g, a.tab, tout);
-  return nd * (dg * invv_cell * invn);
+  return nd_thick * (dg * (__ldg(&ge->invv) * __ldg(invn)));
 }
 
 // Interpolated column (Eq. interp) with optical-depth-modulated weights

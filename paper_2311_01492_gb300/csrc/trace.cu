@@ -221,9 +221,8 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
         } else {
           const GeoEntry* ge = &a.geo[gbase + ((max(a1, a2) * (max(a1, a2) + 1)) >> 1) + min(a1, a2)];
           const double dcell = dtp * ds;
-          const double dG = cell_rate(a, nd, tin, tout, dcell, __ldg(&ge->invv) * B.inv_cell3,
-                                      __ldg(&ge->thin) * B.thin_fac,
-                                      bits_of(dcell) <= bits_of(a.tau_lim) ? 0.0 : __ldg(&a.invn[cell]));
+          const double dG = cell_rate(a, nd * B.inv_cell3, nd * B.thin_fac, tin, tout, dcell, ge,
+                                      &a.invn[cell]);
           ++nrate;
           if (dG != 0.0) atomicAdd(&a.gamma[cell], dG);
         }
@@ -479,9 +478,8 @@ __device__ __forceinline__ void trace_face_whole(const TraceArgs& a, const int i
         } else {
           const GeoEntry* ge = &a.geo[gbase + ((max(a1, a2) * (max(a1, a2) + 1)) >> 1) + min(a1, a2)];
           const double dcell = dtp * ds;
-          const double dG = cell_rate(a, nd, tin, tout, dcell, __ldg(&ge->invv) * B.inv_cell3,
-                                      __ldg(&ge->thin) * B.thin_fac,
-                                      bits_of(dcell) <= bits_of(a.tau_lim) ? 0.0 : __ldg(&a.invn[cell]));
+          const double dG = cell_rate(a, nd * B.inv_cell3, nd * B.thin_fac, tin, tout, dcell, ge,
+                                      &a.invn[cell]);
           ++nrate;
           if (dG != 0.0) atomicAdd(&a.gamma[cell], dG);
         }
@@ -777,9 +775,8 @@ __global__ void __launch_bounds__(BLOCK) k_trace_shells(TraceArgs a) {
           a.coldens[cell] = tout / a.sigma0;
         } else if (bits_of(tin) < a.tab.tau_max_bits) {
           const double dcell = dtp * ds;
-          const double dG = cell_rate(a, nd, tin, tout, dcell, __ldg(&ge->invv) * B.inv_cell3,
-                                      __ldg(&ge->thin) * B.thin_fac,
-                                      bits_of(dcell) <= bits_of(a.tau_lim) ? 0.0 : __ldg(&a.invn[cell]));
+          const double dG = cell_rate(a, nd * B.inv_cell3, nd * B.thin_fac, tin, tout, dcell, ge,
+                                      &a.invn[cell]);
           ++nrate;
           if (dG != 0.0) atomicAdd(&a.gamma[cell], dG);
         }
