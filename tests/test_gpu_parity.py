@@ -258,7 +258,8 @@ def test_no_sources_gives_zero_rates():
     g.close()
 
 
-def test_ensemble_matches_per_box_oracle():
+@pytest.mark.parametrize("interp", [0, 1])
+def test_ensemble_matches_per_box_oracle(interp):
     sizes = [12, 17, 20, 9]
     boxes = [_random_box(n, 6 + b, 9.0, 10 + b, dup=False) for b, n in enumerate(sizes)]
     cell = boxes[0]["cell_cm"]
@@ -270,11 +271,14 @@ def test_ensemble_matches_per_box_oracle():
     R = np.concatenate([b["radius"] for b in boxes])
     bid = np.concatenate([np.full(len(b["pos"]), i) for i, b in enumerate(boxes)])
     g = make_gpu(None, cell, nH, xHI, pos, ndot, R, tab, box=bid, sizes=sizes)
-    for sch in ("batched", "plain"):
+    if interp:
+        g.set_interpolation("optical_depth", 0.6)
+    for sch in ("batched", "plain", "early_exit"):
         gam = g.raytrace(schedule=sch).cpu().numpy()
         off = 0
         for b, bx in zip(sizes, boxes):
-            ref = O.raytrace(b, cell, bx["nH"], bx["xHI"], bx["pos"], bx["ndot"], bx["radius"], tab)
+            ref = O.raytrace(b, cell, bx["nH"], bx["xHI"], bx["pos"], bx["ndot"], bx["radius"], tab,
+                             interp=interp)
             assert_gamma(gam[off:off + b ** 3], ref["gamma"])
             off += b ** 3
     g.stats()
