@@ -35,6 +35,7 @@
 // (2h+1)^2 layer updated in place, every cell of a face computed once.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "asora_internal.cuh"
 #include "device_util.cuh"
@@ -170,64 +171,74 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
     const GeoRow* __restrict__ grow = a.georow + georow_index(m, 0, 0);
     const int gbase = (int)geo_index(m, 0, 0);
     bool opaque = true;  // every cell of this thread has tau_out >= the exit bound
-    for (int t0 = GS == 32 ? total - 1 : gt; GS == 32 ? t0 >= 0 : t0 < total;
-         t0 += GS == 32 ? -32 : GS) {
-      // warp mode: lanes take t0, t0-1, ..., t0-31; lanes below 0 recompute cell 0
-      // and write nothing
-      const int t = GS == 32 ? max(t0 - lane, 0) : t0;
-      const int a1 = rowof[t];
-      const int a2 = t - rowpre[a1];
-      const int x1 = wrapc(c1 + q1 * a1, N), x2 = wrapc(c2 + q2 * a2, N);
-      const int gidx = lay + x1 * m1 + x2;
-      const double dtp = __ldg(&fld[gidx]);
-      const GeoRow* gr = grow + a1 * (m + 1) + a2;
-      const double2 wv0 = __ldg(reinterpret_cast<const double2*>(gr));      // w1, w2
-      const double2 wv1 = __ldg(reinterpret_cast<const double2*>(gr) + 1);  // w3, w4
-      const double ds = __ldg(&gr->ds);
-      double tin;
-      if (m == 1) {
-        tin = (0.5 * dts) * ds;
-      } else {
-        const double w1 = wv0.x, w2 = wv0.y, w3 = wv1.x, w4 = wv1.y;
-        const int b1 = min(a1, Hp), b2 = min(a1 - (a1 > 0), Hp);
-        const int e1 = min(a2, Hp), e2 = min(a2 - (a2 > 0), Hp);
-        const double v1 = prev[b1 * Wp + e1];
-        const double v2 = prev[b2 * Wp + e1];
-        const double v3 = prev[b1 * Wp + e2];
-        const double v4 = prev[b2 * Wp + e2];
-        // w1*v1 as fma(w1, v1, -0.0): the same value for every input (the sum of the
-        // exact product and -0 rounds like the product alone, and +0 + -0 = +0), on
-        // GB300 issued as a DFMA, which retires at least as fast as a DMUL
-        if (OD)
-          tin = od_interp(w1, w2, w3, w4, v1, v2, v3, v4, a.tau_w0, a.neg_zero);
-        else
-          tin = fma(w4, v4, fma(w3, v3, fma(w2, v2, fma(w1, v1, a.neg_zero))));
-      }
-      const double tout = fma(dtp, ds, tin);
-      if (GS == 32) {
-        __syncwarp();  // every lane has read layer m-1 before any lane writes
-        if (t0 - lane < 0) continue;
-      }
-      cur[a1 * W + a2] = tout;
-      opaque = opaque && bits_of(tout) >= a.exit_bits;
-      const bool own = ((d == 2) || (d == 1 ? a2 < m : (a1 < m && a2 < m))) &&
-                       (a1 > 0 || q1 > 0) && (a2 > 0 || q2 > 0);
-      if (!own) continue;
-      if (COLDENS || bits_of(tin) < a.tab.tau_max_bits) {
-        // C-order index of the cell (the z faces gathered from the rotated copy)
-        const int64_t cell = B.off + (d == 2 ? (x1 * N + x2) * N + lc : gidx);
-        if (COLDENS) {
-          a.coldens[cell] = tout / a.sigma0;
+    // Layer 1 takes its column from the source cell alone.  It runs as its own
+    // instantiation of the cell loop: a branch on m inside the loop becomes a
+    // predicated FP64 product in every round of every layer, and an FP64
+    // instruction whose lanes are all predicated off still takes its full turn
+    // on the FP64 pipe.
+    auto cells = [&](auto first) {
+      constexpr bool FIRST = decltype(first)::value;
+      for (int t0 = GS == 32 ? total - 1 : gt; GS == 32 ? t0 >= 0 : t0 < total;
+           t0 += GS == 32 ? -32 : GS) {
+        // warp mode: lanes take t0, t0-1, ..., t0-31; lanes below 0 recompute cell 0
+        // and write nothing
+        const int t = GS == 32 ? max(t0 - lane, 0) : t0;
+        const int a1 = rowof[t];
+        const int a2 = t - rowpre[a1];
+        const int x1 = wrapc(c1 + q1 * a1, N), x2 = wrapc(c2 + q2 * a2, N);
+        const int gidx = lay + x1 * m1 + x2;
+        const double dtp = __ldg(&fld[gidx]);
+        const GeoRow* gr = grow + a1 * (m + 1) + a2;
+        const double2 wv0 = __ldg(reinterpret_cast<const double2*>(gr));      // w1, w2
+        const double2 wv1 = __ldg(reinterpret_cast<const double2*>(gr) + 1);  // w3, w4
+        const double ds = __ldg(&gr->ds);
+        double tin;
+        if constexpr (FIRST) {
+          tin = (0.5 * dts) * ds;
         } else {
-          const GeoEntry* ge = &a.geo[gbase + ((max(a1, a2) * (max(a1, a2) + 1)) >> 1) + min(a1, a2)];
-          const double dcell = dtp * ds;
-          const double dG = cell_rate(a, nd * B.inv_cell3, nd * B.thin_fac, tin, tout, dcell, ge,
-                                      &a.invn[cell]);
-          ++nrate;
-          if (dG != 0.0) atomicAdd(&a.gamma[cell], dG);
+          const double w1 = wv0.x, w2 = wv0.y, w3 = wv1.x, w4 = wv1.y;
+          const int b1 = min(a1, Hp), b2 = min(a1 - (a1 > 0), Hp);
+          const int e1 = min(a2, Hp), e2 = min(a2 - (a2 > 0), Hp);
+          const double v1 = prev[b1 * Wp + e1];
+          const double v2 = prev[b2 * Wp + e1];
+          const double v3 = prev[b1 * Wp + e2];
+          const double v4 = prev[b2 * Wp + e2];
+          // w1*v1 as fma(w1, v1, -0.0): the same value for every input (the sum of the
+          // exact product and -0 rounds like the product alone, and +0 + -0 = +0), on
+          // GB300 issued as a DFMA, which retires at least as fast as a DMUL
+          if (OD)
+            tin = od_interp(w1, w2, w3, w4, v1, v2, v3, v4, a.tau_w0, a.neg_zero);
+          else
+            tin = fma(w4, v4, fma(w3, v3, fma(w2, v2, fma(w1, v1, a.neg_zero))));
+        }
+        const double tout = fma(dtp, ds, tin);
+        if (GS == 32) {
+          __syncwarp();  // every lane has read layer m-1 before any lane writes
+          if (t0 - lane < 0) continue;
+        }
+        cur[a1 * W + a2] = tout;
+        opaque = opaque && bits_of(tout) >= a.exit_bits;
+        const bool own = ((d == 2) || (d == 1 ? a2 < m : (a1 < m && a2 < m))) &&
+                         (a1 > 0 || q1 > 0) && (a2 > 0 || q2 > 0);
+        if (!own) continue;
+        if (COLDENS || bits_of(tin) < a.tab.tau_max_bits) {
+          // C-order index of the cell (the z faces gathered from the rotated copy)
+          const int64_t cell = B.off + (d == 2 ? (x1 * N + x2) * N + lc : gidx);
+          if (COLDENS) {
+            a.coldens[cell] = tout / a.sigma0;
+          } else {
+            const GeoEntry* ge = &a.geo[gbase + ((max(a1, a2) * (max(a1, a2) + 1)) >> 1) + min(a1, a2)];
+            const double dcell = dtp * ds;
+            const double dG = cell_rate(a, nd * B.inv_cell3, nd * B.thin_fac, tin, tout, dcell, ge,
+                                        &a.invn[cell]);
+            ++nrate;
+            if (dG != 0.0) atomicAdd(&a.gamma[cell], dG);
+          }
         }
       }
-    }
+    };
+    if (m == 1) cells(std::true_type());
+    else cells(std::false_type());
     if (m < Lmax && Hn <= h) {  // row tables of the next layer
       if (toff) {
         cp_async_wait_all();
@@ -425,66 +436,72 @@ __device__ __forceinline__ void trace_face_whole(const TraceArgs& a, const int i
     const GeoRow* __restrict__ grow = a.georow + georow_index(m, 0, 0);
     const int gbase = (int)geo_index(m, 0, 0);
     bool opaque = true;  // every cell of this thread has tau_out >= the exit bound
-    for (int j0 = 0; j0 < total; j0 += GS) {
-      const int j = j0 + gt;  // threads past the end recompute the last cell, write nothing
-      int t1, t2, cls;
-      face_cell(min(j, total - 1), m, nEr, nE, nI, LA, rowpre, rowof, t1, t2, cls);
-      const int a1 = abs(t1), a2 = abs(t2);
-      const int x1 = wrapc(c1 + t1, N), x2 = wrapc(c2 + t2, N);
-      const int gidx = lay + x1 * m1 + x2;
-      const double dtp = __ldg(&fld[gidx]);
-      const GeoRow* gr = grow + a1 * (m + 1) + a2;
-      const double2 wv0 = __ldg(reinterpret_cast<const double2*>(gr));      // w1, w2
-      const double2 wv1 = __ldg(reinterpret_cast<const double2*>(gr) + 1);  // w3, w4
-      const double ds = __ldg(&gr->ds);
-      const int o1 = t1 * W + t2;              // slots of (t1, t2), (t1-s1, t2),
-      const int o2 = o1 - sgn_i(t1) * W;       // (t1, t2-s2), (t1-s1, t2-s2)
-      const int o3 = o1 - sgn_i(t2);
-      const int o4 = o2 - sgn_i(t2);
-      double tin;
-      if (m == 1) {
-        tin = half_dts * ds;
-      } else if (OD) {
-        tin = od_interp(wv0.x, wv0.y, wv1.x, wv1.y, ctr[o1], ctr[o2], ctr[o3], ctr[o4], a.tau_w0,
-                        a.neg_zero);
-      } else if (__all_sync(0xffffffffu, cls != CLS_I)) {
-        // rim row (w1 = w3 = 0), rim column (w1 = w2 = 0), axis t1 = 0 (w2 = w4 = 0),
-        // axis t2 = 0 (w3 = w4 = 0)
-        const bool er = cls == CLS_EROW, ec = cls == CLS_ECOL, rim = er || ec;
-        const double wA = er ? wv0.y : (ec ? wv1.x : wv0.x);
-        const int oA = er ? o2 : (ec ? o3 : o1);
-        const double wB = rim ? wv1.y : (cls == CLS_AT1 ? wv1.x : wv0.y);
-        const int oB = rim ? o4 : (cls == CLS_AT1 ? o3 : o2);
-        tin = fma(wB, ctr[oB], fma(wA, ctr[oA], a.neg_zero));
-      } else {
-        // w1*c1 as fma(w1, c1, -0.0): the same value for every input (the sum of the
-        // exact product and -0 rounds like the product alone, and +0 + -0 = +0), on
-        // GB300 issued as a DFMA, which retires at least as fast as a DMUL
-        tin = fma(wv1.y, ctr[o4], fma(wv1.x, ctr[o3], fma(wv0.y, ctr[o2],
-                                                           fma(wv0.x, ctr[o1], a.neg_zero))));
-      }
-      const double tout = fma(dtp, ds, tin);
-      group_sync<GS>();  // every thread has read layer m-1 before any thread writes
-      if (j >= total) continue;
-      ctr[o1] = tout;
-      opaque = opaque && bits_of(tout) >= a.exit_bits;
-      const bool own = (d == 2) || (d == 1 ? a2 < m : (a1 < m && a2 < m));
-      if (!own) continue;
-      if (COLDENS || bits_of(tin) < a.tab.tau_max_bits) {
-        // C-order index of the cell (the z faces gathered from the rotated copy)
-        const int64_t cell = B.off + (d == 2 ? (x1 * N + x2) * N + lc : gidx);
-        if (COLDENS) {
-          a.coldens[cell] = tout / a.sigma0;
+    // layer 1 as its own instantiation of the cell loop, as in trace_face_item
+    auto cells = [&](auto first) {
+      constexpr bool FIRST = decltype(first)::value;
+      for (int j0 = 0; j0 < total; j0 += GS) {
+        const int j = j0 + gt;  // threads past the end recompute the last cell, write nothing
+        int t1, t2, cls;
+        face_cell(min(j, total - 1), m, nEr, nE, nI, LA, rowpre, rowof, t1, t2, cls);
+        const int a1 = abs(t1), a2 = abs(t2);
+        const int x1 = wrapc(c1 + t1, N), x2 = wrapc(c2 + t2, N);
+        const int gidx = lay + x1 * m1 + x2;
+        const double dtp = __ldg(&fld[gidx]);
+        const GeoRow* gr = grow + a1 * (m + 1) + a2;
+        const double2 wv0 = __ldg(reinterpret_cast<const double2*>(gr));      // w1, w2
+        const double2 wv1 = __ldg(reinterpret_cast<const double2*>(gr) + 1);  // w3, w4
+        const double ds = __ldg(&gr->ds);
+        const int o1 = t1 * W + t2;              // slots of (t1, t2), (t1-s1, t2),
+        const int o2 = o1 - sgn_i(t1) * W;       // (t1, t2-s2), (t1-s1, t2-s2)
+        const int o3 = o1 - sgn_i(t2);
+        const int o4 = o2 - sgn_i(t2);
+        double tin;
+        if constexpr (FIRST) {
+          tin = half_dts * ds;
+        } else if (OD) {
+          tin = od_interp(wv0.x, wv0.y, wv1.x, wv1.y, ctr[o1], ctr[o2], ctr[o3], ctr[o4], a.tau_w0,
+                          a.neg_zero);
+        } else if (__all_sync(0xffffffffu, cls != CLS_I)) {
+          // rim row (w1 = w3 = 0), rim column (w1 = w2 = 0), axis t1 = 0 (w2 = w4 = 0),
+          // axis t2 = 0 (w3 = w4 = 0)
+          const bool er = cls == CLS_EROW, ec = cls == CLS_ECOL, rim = er || ec;
+          const double wA = er ? wv0.y : (ec ? wv1.x : wv0.x);
+          const int oA = er ? o2 : (ec ? o3 : o1);
+          const double wB = rim ? wv1.y : (cls == CLS_AT1 ? wv1.x : wv0.y);
+          const int oB = rim ? o4 : (cls == CLS_AT1 ? o3 : o2);
+          tin = fma(wB, ctr[oB], fma(wA, ctr[oA], a.neg_zero));
         } else {
-          const GeoEntry* ge = &a.geo[gbase + ((max(a1, a2) * (max(a1, a2) + 1)) >> 1) + min(a1, a2)];
-          const double dcell = dtp * ds;
-          const double dG = cell_rate(a, nd * B.inv_cell3, nd * B.thin_fac, tin, tout, dcell, ge,
-                                      &a.invn[cell]);
-          ++nrate;
-          if (dG != 0.0) atomicAdd(&a.gamma[cell], dG);
+          // w1*c1 as fma(w1, c1, -0.0): the same value for every input (the sum of the
+          // exact product and -0 rounds like the product alone, and +0 + -0 = +0), on
+          // GB300 issued as a DFMA, which retires at least as fast as a DMUL
+          tin = fma(wv1.y, ctr[o4], fma(wv1.x, ctr[o3], fma(wv0.y, ctr[o2],
+                                                             fma(wv0.x, ctr[o1], a.neg_zero))));
+        }
+        const double tout = fma(dtp, ds, tin);
+        group_sync<GS>();  // every thread has read layer m-1 before any thread writes
+        if (j >= total) continue;
+        ctr[o1] = tout;
+        opaque = opaque && bits_of(tout) >= a.exit_bits;
+        const bool own = (d == 2) || (d == 1 ? a2 < m : (a1 < m && a2 < m));
+        if (!own) continue;
+        if (COLDENS || bits_of(tin) < a.tab.tau_max_bits) {
+          // C-order index of the cell (the z faces gathered from the rotated copy)
+          const int64_t cell = B.off + (d == 2 ? (x1 * N + x2) * N + lc : gidx);
+          if (COLDENS) {
+            a.coldens[cell] = tout / a.sigma0;
+          } else {
+            const GeoEntry* ge = &a.geo[gbase + ((max(a1, a2) * (max(a1, a2) + 1)) >> 1) + min(a1, a2)];
+            const double dcell = dtp * ds;
+            const double dG = cell_rate(a, nd * B.inv_cell3, nd * B.thin_fac, tin, tout, dcell, ge,
+                                        &a.invn[cell]);
+            ++nrate;
+            if (dG != 0.0) atomicAdd(&a.gamma[cell], dG);
+          }
         }
       }
-    }
+    };
+    if (m == 1) cells(std::true_type());
+    else cells(std::false_type());
     if (m < Lmax && Hn <= h) cp_async_wait_all();
     if (exit_ok) {
       // exact early exit, as in trace_face_item
