@@ -93,10 +93,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index, folder):
+    def __init__(self, index, folder, name="clocks_bench.csv"):
         self.index = index
         self.proc = None
-        self.path = os.path.join(folder, "clocks_bench.csv")
+        self.path = os.path.join(folder, name)
 
     def start(self):
         try:
@@ -381,6 +381,63 @@ def main():
     value = w["paper_sv"] / (ms * 1e-3)  # the whole catalogue's source-voxels per step
     tr_ms = statistics.mean(trace_ms)
 
+    # ---------------- end to end through the public API with host buffers, right after
+    # the device-resident steps (same clocks and thermal state)
+    pin = dict(pin_memory=True)
+    h_nH = torch.tensor(w["nH"].reshape(-1), dtype=torch.float64).pin_memory()
+    h_xHI = torch.tensor(w["xHI"].reshape(-1), dtype=torch.float64).pin_memory()
+    h_pos = torch.tensor(pos, dtype=torch.int32).pin_memory()
+    h_ndot = torch.tensor(ndot, dtype=torch.float64).pin_memory()
+    h_R = torch.tensor(radius, dtype=torch.float64).pin_memory()
+    h_gamma = torch.empty(n ** 3, dtype=torch.float64, **pin)
+    h_cnt = torch.empty(1, dtype=torch.int64, **pin)
+    e2e_in = [h_nH, h_xHI, h_pos, h_ndot, h_R]
+    h2d = sum(t.numel() * t.element_size() for t in e2e_in)
+    d2h = h_gamma.numel() * 8 + 8
+    nH2 = torch.empty_like(nH_d)
+    xHI2 = torch.empty_like(xHI_d)
+    pos2 = torch.empty_like(pos_d)
+    ndot2 = torch.empty_like(ndot_d)
+    R2 = torch.empty_like(R_d)
+    x02 = torch.empty_like(x0_d)
+
+    def e2e_trace(gam):
+        nH2.copy_(h_nH, non_blocking=True)
+        xHI2.copy_(h_xHI, non_blocking=True)
+        pos2.copy_(h_pos, non_blocking=True)
+        ndot2.copy_(h_ndot, non_blocking=True)
+        R2.copy_(h_R, non_blocking=True)
+        g.set_density(nH2)
+        g.set_xHI(xHI2)
+        g.set_sources(pos2, ndot2, R2)
+        g.raytrace(gam, schedule="batched")
+
+    def e2e_chemistry(gam):
+        torch.sub(1.0, xHI2, out=x02)
+        xa, xn, cnt = g.chemistry_step(gam, x02, x02, dt)
+        h_gamma.copy_(gam, non_blocking=True)
+        h_cnt.copy_(cnt, non_blocking=True)
+
+    e2e_step = SH.ShardedStep(e2e_trace, e2e_chemistry, dist, world)
+    e2e_step(gamma)
+    torch.cuda.synchronize()
+    e_ms = []
+    e2e_sampler = ClockSampler(local, scratch, "clocks_e2e.csv")
+    e2e_sampler.start()
+    for _ in range(args.steps):
+        flush.fill_(2.0)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        e2e_step(gamma)
+        torch.cuda.synchronize()
+        e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_clocks = e2e_sampler.stop()
+    e2e_ms = statistics.mean(e_ms)
+    if world > 1:
+        e2e_ms, _ = SH.aggregate(e2e_ms, my_sv, dist, device=dev)
+
     # ---------------- plain (ASORA-style block-per-source) comparison
     plain = None
     if args.plain_steps > 0:
@@ -506,59 +563,6 @@ def main():
         box128 = extra_box128(dev, flush, os.path.join(scratch, "autotune_box128.txt"))
         ensemble = extra_ensemble(dev, flush, os.path.join(scratch, "autotune_ensemble.txt"))
 
-    # ---------------- end to end through the public API with host buffers
-    pin = dict(pin_memory=True)
-    h_nH = torch.tensor(w["nH"].reshape(-1), dtype=torch.float64).pin_memory()
-    h_xHI = torch.tensor(w["xHI"].reshape(-1), dtype=torch.float64).pin_memory()
-    h_pos = torch.tensor(pos, dtype=torch.int32).pin_memory()
-    h_ndot = torch.tensor(ndot, dtype=torch.float64).pin_memory()
-    h_R = torch.tensor(radius, dtype=torch.float64).pin_memory()
-    h_gamma = torch.empty(n ** 3, dtype=torch.float64, **pin)
-    h_cnt = torch.empty(1, dtype=torch.int64, **pin)
-    e2e_in = [h_nH, h_xHI, h_pos, h_ndot, h_R]
-    h2d = sum(t.numel() * t.element_size() for t in e2e_in)
-    d2h = h_gamma.numel() * 8 + 8
-    nH2 = torch.empty_like(nH_d)
-    xHI2 = torch.empty_like(xHI_d)
-    pos2 = torch.empty_like(pos_d)
-    ndot2 = torch.empty_like(ndot_d)
-    R2 = torch.empty_like(R_d)
-    x02 = torch.empty_like(x0_d)
-
-    def e2e_trace(gam):
-        nH2.copy_(h_nH, non_blocking=True)
-        xHI2.copy_(h_xHI, non_blocking=True)
-        pos2.copy_(h_pos, non_blocking=True)
-        ndot2.copy_(h_ndot, non_blocking=True)
-        R2.copy_(h_R, non_blocking=True)
-        g.set_density(nH2)
-        g.set_xHI(xHI2)
-        g.set_sources(pos2, ndot2, R2)
-        g.raytrace(gam, schedule="batched")
-
-    def e2e_chemistry(gam):
-        torch.sub(1.0, xHI2, out=x02)
-        xa, xn, cnt = g.chemistry_step(gam, x02, x02, dt)
-        h_gamma.copy_(gam, non_blocking=True)
-        h_cnt.copy_(cnt, non_blocking=True)
-
-    e2e_step = SH.ShardedStep(e2e_trace, e2e_chemistry, dist, world)
-    e2e_step(gamma)
-    torch.cuda.synchronize()
-    e_ms = []
-    for _ in range(args.steps):
-        flush.fill_(2.0)
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        t0 = time.perf_counter()
-        e2e_step(gamma)
-        torch.cuda.synchronize()
-        e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_ms = statistics.mean(e_ms)
-    if world > 1:
-        e2e_ms, _ = SH.aggregate(e2e_ms, my_sv, dist, device=dev)
-
     # ---------------- roofline of the dominant kernel (the batched trace)
     flops = FP64_FLOPS_PER_SV * exact_sv + FP64_FLOPS_PER_RATE * statistics.mean(rate_cells)
     achieved_tf = flops / (tr_ms * 1e-3) / 1e12
@@ -635,7 +639,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": w["paper_sv"] / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                    "steps": args.steps},
+                    "steps": args.steps, "clocks": e2e_clocks},
             "gpu_launches": launches // max(1, args.steps),
             "gpu_launches_note": "library kernels per step (+ CUB radix-sort/scan kernels of the "
                                  "source ingest)",

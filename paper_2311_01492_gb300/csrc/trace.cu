@@ -726,78 +726,86 @@ __global__ void __launch_bounds__(BLOCK) k_trace_shells(TraceArgs a) {
     const int Q = min(3 * emax, isqrt_i(3 * R2));
     for (int q = 0; q <= Q; ++q) {
       const int cnt = q == 0 ? 1 : 4 * q * q + 2;
-      for (int t = tid; t < cnt; t += BLOCK) {
-        int di, dj, dk;
-        shell_cell(q, t, di, dj, dk);
-        if (di < B.wlo || di > B.whi || dj < B.wlo || dj > B.whi || dk < B.wlo || dk > B.whi)
-          continue;
-        const int d2 = di * di + dj * dj + dk * dk;
-        if (d2 > R2) continue;
-        const int ii = wrapc(S.i + di, N), jj = wrapc(S.j + dj, N), kk = wrapc(S.k + dk, N);
-        const int64_t cell = B.off + ((int64_t)ii * N + jj) * N + kk;
-        if (q == 0) {
-          const double tout = 0.5 * dts;
-          cube[cidx(0, 0, 0)] = tout;
+      // Cells with max|Delta| = 1 (and the source cell) lie in shells q <= 3 only;
+      // the later shells run an instantiation without those branches, which would
+      // otherwise issue FP64 products with every lane predicated off.
+      auto cells = [&](auto near) {
+        constexpr bool NEAR = decltype(near)::value;
+        for (int t = tid; t < cnt; t += BLOCK) {
+          int di, dj, dk;
+          shell_cell(q, t, di, dj, dk);
+          if (di < B.wlo || di > B.whi || dj < B.wlo || dj > B.whi || dk < B.wlo || dk > B.whi)
+            continue;
+          const int d2 = di * di + dj * dj + dk * dk;
+          if (d2 > R2) continue;
+          const int ii = wrapc(S.i + di, N), jj = wrapc(S.j + dj, N), kk = wrapc(S.k + dk, N);
+          const int64_t cell = B.off + ((int64_t)ii * N + jj) * N + kk;
+          if (NEAR && q == 0) {
+            const double tout = 0.5 * dts;
+            cube[cidx(0, 0, 0)] = tout;
+            if (a.coldens) {
+              a.coldens[cell] = tout / a.sigma0;
+            } else {
+              double dG;
+              if (bits_of(tout) <= bits_of(a.tau_lim))
+                dG = nd * (tab_eval(a.tab.h, a.tab, 0.0) * (0.5 * B.thin_fac));
+              else
+                dG = nd * ((tab_eval(a.tab.g, a.tab, 0.0) - tab_eval(a.tab.g, a.tab, tout)) *
+                           B.inv_cell3 * a.invn[cell]);
+              if (dG != 0.0) atomicAdd(&a.gamma[cell], dG);
+            }
+            continue;
+          }
+          const int adi = abs(di), adj = abs(dj), adk = abs(dk);
+          const int m = max(adi, max(adj, adk));
+          int D[3] = {di, dj, dk};
+          int ax, x1, x2;
+          if (adk == m) { ax = 2; x1 = 0; x2 = 1; }
+          else if (adj == m) { ax = 1; x1 = 0; x2 = 2; }
+          else { ax = 0; x1 = 1; x2 = 2; }
+          const int p1 = D[x1], p2 = D[x2];
+          const int ap1 = abs(p1), ap2 = abs(p2);
+          const GeoEntry* ge = &a.geo[geo_index(m, min(ap1, ap2), max(ap1, ap2))];
+          const double w1 = __ldg(&ge->w1), w4 = __ldg(&ge->w4), ds = __ldg(&ge->ds);
+          const double w2 = ap1 <= ap2 ? __ldg(&ge->wa) : __ldg(&ge->wb);
+          const double w3 = ap1 <= ap2 ? __ldg(&ge->wb) : __ldg(&ge->wa);
+          double tin;
+          if (NEAR && m == 1) {
+            tin = (0.5 * dts) * ds;
+          } else {
+            int e1[3] = {di, dj, dk};
+            e1[ax] -= sgn_i(D[ax]);
+            int e2[3] = {e1[0], e1[1], e1[2]};
+            e2[x1] -= sgn_i(p1);
+            int e3[3] = {e1[0], e1[1], e1[2]};
+            e3[x2] -= sgn_i(p2);
+            int e4[3] = {e2[0], e2[1], e2[2]};
+            e4[x2] -= sgn_i(p2);
+            const double c1 = cube[cidx(e1[0], e1[1], e1[2])];
+            const double c2 = cube[cidx(e2[0], e2[1], e2[2])];
+            const double c3 = cube[cidx(e3[0], e3[1], e3[2])];
+            const double c4 = cube[cidx(e4[0], e4[1], e4[2])];
+            if (OD)
+              tin = od_interp(w1, w2, w3, w4, c1, c2, c3, c4, a.tau_w0, a.neg_zero);
+            else
+              tin = fma(w4, c4, fma(w3, c3, fma(w2, c2, w1 * c1)));
+          }
+          const double dtp = __ldg(&a.dtau[cell]);
+          const double tout = fma(dtp, ds, tin);
+          cube[cidx(di, dj, dk)] = tout;
           if (a.coldens) {
             a.coldens[cell] = tout / a.sigma0;
-          } else {
-            double dG;
-            if (bits_of(tout) <= bits_of(a.tau_lim))
-              dG = nd * (tab_eval(a.tab.h, a.tab, 0.0) * (0.5 * B.thin_fac));
-            else
-              dG = nd * ((tab_eval(a.tab.g, a.tab, 0.0) - tab_eval(a.tab.g, a.tab, tout)) *
-                         B.inv_cell3 * a.invn[cell]);
+          } else if (bits_of(tin) < a.tab.tau_max_bits) {
+            const double dcell = dtp * ds;
+            const double dG = cell_rate(a, nd * B.inv_cell3, nd * B.thin_fac, tin, tout, dcell, ge,
+                                        &a.invn[cell]);
+            ++nrate;
             if (dG != 0.0) atomicAdd(&a.gamma[cell], dG);
           }
-          continue;
         }
-        const int adi = abs(di), adj = abs(dj), adk = abs(dk);
-        const int m = max(adi, max(adj, adk));
-        int D[3] = {di, dj, dk};
-        int ax, x1, x2;
-        if (adk == m) { ax = 2; x1 = 0; x2 = 1; }
-        else if (adj == m) { ax = 1; x1 = 0; x2 = 2; }
-        else { ax = 0; x1 = 1; x2 = 2; }
-        const int p1 = D[x1], p2 = D[x2];
-        const int ap1 = abs(p1), ap2 = abs(p2);
-        const GeoEntry* ge = &a.geo[geo_index(m, min(ap1, ap2), max(ap1, ap2))];
-        const double w1 = __ldg(&ge->w1), w4 = __ldg(&ge->w4), ds = __ldg(&ge->ds);
-        const double w2 = ap1 <= ap2 ? __ldg(&ge->wa) : __ldg(&ge->wb);
-        const double w3 = ap1 <= ap2 ? __ldg(&ge->wb) : __ldg(&ge->wa);
-        double tin;
-        if (m == 1) {
-          tin = (0.5 * dts) * ds;
-        } else {
-          int e1[3] = {di, dj, dk};
-          e1[ax] -= sgn_i(D[ax]);
-          int e2[3] = {e1[0], e1[1], e1[2]};
-          e2[x1] -= sgn_i(p1);
-          int e3[3] = {e1[0], e1[1], e1[2]};
-          e3[x2] -= sgn_i(p2);
-          int e4[3] = {e2[0], e2[1], e2[2]};
-          e4[x2] -= sgn_i(p2);
-          const double c1 = cube[cidx(e1[0], e1[1], e1[2])];
-          const double c2 = cube[cidx(e2[0], e2[1], e2[2])];
-          const double c3 = cube[cidx(e3[0], e3[1], e3[2])];
-          const double c4 = cube[cidx(e4[0], e4[1], e4[2])];
-          if (OD)
-            tin = od_interp(w1, w2, w3, w4, c1, c2, c3, c4, a.tau_w0, a.neg_zero);
-          else
-            tin = fma(w4, c4, fma(w3, c3, fma(w2, c2, w1 * c1)));
-        }
-        const double dtp = __ldg(&a.dtau[cell]);
-        const double tout = fma(dtp, ds, tin);
-        cube[cidx(di, dj, dk)] = tout;
-        if (a.coldens) {
-          a.coldens[cell] = tout / a.sigma0;
-        } else if (bits_of(tin) < a.tab.tau_max_bits) {
-          const double dcell = dtp * ds;
-          const double dG = cell_rate(a, nd * B.inv_cell3, nd * B.thin_fac, tin, tout, dcell, ge,
-                                      &a.invn[cell]);
-          ++nrate;
-          if (dG != 0.0) atomicAdd(&a.gamma[cell], dG);
-        }
-      }
+      };
+      if (q <= 3) cells(std::true_type());
+      else cells(std::false_type());
       __syncthreads();  // shell q complete before shell q+1 reads it
     }
   }
