@@ -171,6 +171,7 @@ __device__ __forceinline__ void bwd_item(const BwdArgs& A, const int item, const
   double* cur = bufB;
   int Hp = 0, Llast = 0;
   size_t off = 0;
+  if (gt == 0) prev[0] = 0.5 * dts;  // the interpolant of every layer-1 cell
   for (int m = 1; m <= Lmax; ++m) {
     const int rem = R2 - m * m;
     const int H = min(m, isqrt_i(rem));
@@ -200,18 +201,21 @@ __device__ __forceinline__ void bwd_item(const BwdArgs& A, const int item, const
       const double dtp = __ldg(&fld[gidx]);
       const GeoEntry* ge = &a.geo[gbase + ((max(a1, a2) * (max(a1, a2) + 1)) >> 1) + min(a1, a2)];
       const double ds = __ldg(&ge->ds);
-      double tin;
-      if (m == 1) {
-        tin = (0.5 * dts) * ds;
-      } else {
-        const double w1 = __ldg(&ge->w1), w4 = __ldg(&ge->w4);
-        const double w2 = a1 <= a2 ? __ldg(&ge->wa) : __ldg(&ge->wb);
-        const double w3 = a1 <= a2 ? __ldg(&ge->wb) : __ldg(&ge->wa);
-        const int b1 = min(a1, Hp), b2 = min(a1 - (a1 > 0), Hp);
-        const int e1 = min(a2, Hp), e2 = min(a2 - (a2 > 0), Hp);
-        tin = fma(w4, prev[b2 * Wp + e2],
-                  fma(w3, prev[b1 * Wp + e2], fma(w2, prev[b2 * Wp + e1], w1 * prev[b1 * Wp + e1])));
-      }
+      // Layer 1 (tau_in = (dtau_s/2) ds) goes through the same chain, so that no
+      // branch on m turns into an FP64 product issued with every lane predicated
+      // off in the other layers' rounds: its interpolants all read slot 0 of the
+      // previous buffer, which holds dtau_s/2, with weights (ds, 0, 0, 0); the
+      // zero terms add exactly +0.
+      const bool l1 = m == 1;
+      const double wa = __ldg(&ge->wa), wb = __ldg(&ge->wb);
+      const double w1 = l1 ? ds : __ldg(&ge->w1), w4 = l1 ? 0.0 : __ldg(&ge->w4);
+      const double w2 = l1 ? 0.0 : (a1 <= a2 ? wa : wb);
+      const double w3 = l1 ? 0.0 : (a1 <= a2 ? wb : wa);
+      const int b1 = min(a1, Hp), b2 = min(a1 - (a1 > 0), Hp);
+      const int e1 = min(a2, Hp), e2 = min(a2 - (a2 > 0), Hp);
+      const double tin = fma(w4, prev[b2 * Wp + e2],
+                             fma(w3, prev[b1 * Wp + e2], fma(w2, prev[b2 * Wp + e1],
+                                                             w1 * prev[b1 * Wp + e1])));
       const double tout = fma(dtp, ds, tin);
       const int li = a1 * W + a2;
       cur[li] = tout;
@@ -344,7 +348,19 @@ __device__ __forceinline__ void bwd_item(const BwdArgs& A, const int item, const
       nz = nz || mup != 0.0;
       const double contrib = dtp * (lam * ds) + ndir;
       if (contrib != 0.0) atomicAdd(&A.dlogn[cell], contrib);
-      if (m == 1) srcacc += mup * (0.5 * ds);
+    }
+    if (m == 1) {
+      // dL/ddtau(s) from layer 1, after its rounds (kept out of the cell loop so that
+      // no FP64 product runs with every lane off in the other layers): the same
+      // thread takes the same cells as in the loop, so each partial sum is unchanged
+      for (int t = gt; t < total; t += GS) {
+        const int a1 = rowof[t];
+        const int a2 = t - rowpre[a1];
+        const GeoEntry* ge = &a.geo[gbase + ((max(a1, a2) * (max(a1, a2) + 1)) >> 1) + min(a1, a2)];
+        const double mup = mu[a1 * W + a2];
+        if (!(bits_of(mup) << 1)) continue;  // mu = 0: no term (as in the loop)
+        srcacc += mup * (0.5 * __ldg(&ge->ds));
+      }
     }
     nz_next = group_any<GS>(nz);
     double* tmp = next;
