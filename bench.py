@@ -484,7 +484,8 @@ def main():
                "ms_total_replay": it_ms[1], "ms_per_iteration": it_ms[1] / K_IT,
                "note": "one CUDA graph of K iterations, captured on the first call and "
                        "replayed by the second; each iteration = dtau precompute + batched "
-                       "trace + chemistry + convergence count"}
+                       "trace + chemistry + convergence count"
+                       + ("; rank 0's shard of the sources, no exchange" if world > 1 else "")}
 
     # ---------------- rate-heavy variant: the same field with x_HI x 1e-4 (a nearly
     # ionised box as in the paper's Test 3), 1e5 of the sources: Gamma is non-zero over
