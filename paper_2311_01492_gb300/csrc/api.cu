@@ -278,6 +278,7 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
     const int pw = first_fitting(g.hsmall);
     const int p4 = std::max(pw, first_fitting(g.hface));
     const int hbig = face_hcap(r2s[0], g.nmax);
+    const bool od = a.interp_mode == RT_INTERP_OPTICAL_DEPTH;
     TRY(cudaMemsetAsync(g.queue, 0, 3 * sizeof(int), g.stream));
     a.items = items;
     g.stats.launches = 0;
@@ -287,7 +288,7 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
     auto warp_launch = [&](int mode, int hcap, int item_begin, int item_end, int* queue) {
       int wpb = 8, maxg = 0;
       for (int cand = 8; cand >= 1; --cand) {
-        const int mg = faces_max_grid(mode, faces_smem_bytes(hcap, mode) * cand, cand);
+        const int mg = faces_max_grid(mode, faces_smem_bytes(hcap, mode, od) * cand, cand, od);
         if (mg * cand > maxg * wpb) {
           maxg = mg;
           wpb = cand;
@@ -302,7 +303,7 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
       b.queue = queue;
       const int nitem = item_end - item_begin;
       const int grid = std::max(1, std::min((nitem + wpb - 1) / wpb, maxg));
-      TRY(launch_trace_faces(g, b, mode, grid, faces_smem_bytes(hcap, mode) * wpb, wpb));
+      TRY(launch_trace_faces(g, b, mode, grid, faces_smem_bytes(hcap, mode, od) * wpb, wpb));
       g.stats.launches += 1;
       if (g.stats.launches == 1) {
         g.stats.block = 32 * wpb;
@@ -312,11 +313,11 @@ static rt_status run_trace(Grid& g, double* gamma, double* coldens, const int* i
     };
     if (pw > 0) {
       const int block = g.block_big;
-      const size_t smem = faces_smem_bytes(hbig, block);
+      const size_t smem = faces_smem_bytes(hbig, block, od);
       if (smem > 227 * 1024)
         return fail(RT_ERR_INVALID, "rt_raytrace: radius too large for the batched schedule's "
                                     "shared-memory layers; use RT_SCHED_PLAIN");
-      const int maxg = faces_max_grid(block, smem);
+      const int maxg = faces_max_grid(block, smem, 8, od);
       if (maxg <= 0) return fail(RT_ERR_CUDA, "rt_raytrace: no occupancy for the face kernel");
       TraceArgs b = a;
       b.hcap = hbig;

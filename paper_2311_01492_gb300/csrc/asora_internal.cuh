@@ -280,8 +280,9 @@ cudaError_t launch_geometry(GeoEntry* geo, GeoRow* georow, int mmax, cudaStream_
 cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid, size_t smem,
                                int wpb = 8);  // wpb: warps per CTA in warp mode (block 32)
 cudaError_t launch_trace_shells(Grid& g, const TraceArgs& a, int block, int grid);
-size_t faces_smem_bytes(int hcap, int block);  // per CTA (block 32: per warp)
-int faces_max_grid(int block, size_t smem, int wpb = 8);
+// per CTA (block 32, 4: per warp); od: with the reciprocal buffers of mode 1
+size_t faces_smem_bytes(int hcap, int block, bool od = false);
+int faces_max_grid(int block, size_t smem, int wpb = 8, bool od = false);
 int shells_max_grid(int block);
 rt_status ingest_sources(Grid& g, int nsrc, const int32_t* d_pos, const int32_t* d_box,
                          const double* d_ndot, const double* d_radius);

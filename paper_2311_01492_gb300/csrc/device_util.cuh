@@ -54,18 +54,24 @@ __device__ __forceinline__ double cell_rate(const TraceArgs& a, double nd_thick,
 
 // Interpolated column (Eq. interp) with optical-depth-modulated weights
 // (interpolation mode 1, after the C2Ray paper's App. A, to which Sec. 3.1
-// refers for the weighting): each geometric weight times 1/max(c_n, tw0), the
-// sum normalised by the modulated weights, summed in the same order as the
-// geometric chain.
+// refers for the weighting): each geometric weight times r_n = 1/max(c_n, tw0),
+// the sum normalised by the modulated weights, summed in the same order as the
+// geometric chain.  The batched kernels keep r_n beside c_n in shared memory
+// (formed once, when the cell's column is written, instead of once per reader).
+__device__ __forceinline__ double od_interp_r(double w1, double w2, double w3, double w4,
+                                              double c1, double c2, double c3, double c4,
+                                              double r1, double r2, double r3, double r4,
+                                              double nz) {
+  const double v1 = w1 * r1, v2 = w2 * r2, v3 = w3 * r3, v4 = w4 * r4;
+  const double S = ((v1 + v2) + v3) + v4;
+  return fma(v4, c4, fma(v3, c3, fma(v2, c2, fma(v1, c1, nz)))) / S;
+}
+__device__ __forceinline__ double od_recip(double c, double tw0) { return 1.0 / fmax(c, tw0); }
 __device__ __forceinline__ double od_interp(double w1, double w2, double w3, double w4, double c1,
                                             double c2, double c3, double c4, double tw0,
                                             double nz) {
-  const double v1 = w1 * (1.0 / fmax(c1, tw0));
-  const double v2 = w2 * (1.0 / fmax(c2, tw0));
-  const double v3 = w3 * (1.0 / fmax(c3, tw0));
-  const double v4 = w4 * (1.0 / fmax(c4, tw0));
-  const double S = ((v1 + v2) + v3) + v4;
-  return fma(v4, c4, fma(v3, c3, fma(v2, c2, fma(v1, c1, nz)))) / S;
+  return od_interp_r(w1, w2, w3, w4, c1, c2, c3, c4, od_recip(c1, tw0), od_recip(c2, tw0),
+                     od_recip(c3, tw0), od_recip(c4, tw0), nz);
 }
 
 // Slope of the table at tau (derivative of the lookup): the chord slope c1
@@ -95,27 +101,30 @@ __host__ __device__ inline int row_slot_bytes(int h) {
 
 // Shared memory of one group tracing a quadrant of a face with layer half-width
 // capacity h: two layers of (h+1)^2 doubles in CTA mode, one (updated in place)
-// in warp mode, then (16-byte aligned, for cp.async) two row-table slots: the
-// current layer's and the next's.
-__host__ __device__ inline size_t layer_bytes(int h, bool warp) {
+// in warp mode -- with optical-depth-modulated weights (od) followed by as many
+// again for the reciprocals 1/max(tau_out, tau_w0) of the same slots -- then
+// (16-byte aligned, for cp.async) two row-table slots: the current layer's and
+// the next's.
+__host__ __device__ inline size_t layer_bytes(int h, bool warp, bool od = false) {
   const size_t cap = (size_t)(h + 1) * (h + 1);
-  return ((warp ? 1 : 2) * cap * sizeof(double) + 15) & ~(size_t)15;
+  return ((warp ? 1 : 2) * (od ? 2 : 1) * cap * sizeof(double) + 15) & ~(size_t)15;
 }
-__host__ __device__ inline size_t group_smem_bytes(int h, bool warp) {
-  return layer_bytes(h, warp) + 2 * (size_t)row_slot_bytes(h);
+__host__ __device__ inline size_t group_smem_bytes(int h, bool warp, bool od = false) {
+  return layer_bytes(h, warp, od) + 2 * (size_t)row_slot_bytes(h);
 }
 
 // Shared memory of one warp tracing a whole face: the face layer, (2h+1)^2
 // doubles updated in place (slot of transverse offset (t1, t2) at
-// (t1+h)(2h+1) + t2+h), then two slots for the interior row tables (the current
-// layer's and the next's).  At least the single-quadrant warp layout of
-// group_smem_bytes, which faces clipped by the window use instead.
-__host__ __device__ inline size_t face_buf_bytes(int h) {
-  return ((size_t)(2 * h + 1) * (2 * h + 1) * sizeof(double) + 15) & ~(size_t)15;
+// (t1+h)(2h+1) + t2+h; with od, then the reciprocals of the same slots), then
+// two slots for the interior row tables (the current layer's and the next's).
+// At least the single-quadrant warp layout of group_smem_bytes, which faces
+// clipped by the window use instead.
+__host__ __device__ inline size_t face_buf_bytes(int h, bool od = false) {
+  return ((od ? 2 : 1) * (size_t)(2 * h + 1) * (2 * h + 1) * sizeof(double) + 15) & ~(size_t)15;
 }
-__host__ __device__ inline size_t whole_smem_bytes(int h) {
-  const size_t w = face_buf_bytes(h) + 2 * (size_t)row_slot_bytes(h);
-  const size_t q = group_smem_bytes(h, true);
+__host__ __device__ inline size_t whole_smem_bytes(int h, bool od = false) {
+  const size_t w = face_buf_bytes(h, od) + 2 * (size_t)row_slot_bytes(h);
+  const size_t q = group_smem_bytes(h, true, od);
   return w > q ? w : q;
 }
 

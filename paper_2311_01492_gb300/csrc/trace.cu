@@ -44,8 +44,8 @@ namespace asora {
 
 // ----------------------------------------------------------- face kernels
 // block codes: 128/256 CTA mode, 32 warp mode, 4 whole-face warp mode
-size_t faces_smem_bytes(int hcap, int block) {
-  return block == 4 ? whole_smem_bytes(hcap) : group_smem_bytes(hcap, block == 32);
+size_t faces_smem_bytes(int hcap, int block, bool od) {
+  return block == 4 ? whole_smem_bytes(hcap, od) : group_smem_bytes(hcap, block == 32, od);
 }
 
 // Trace one (source, face, quadrant) item with a group of GS threads (gt =
@@ -73,8 +73,9 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
   const int cap = (h + 1) * (h + 1);
   double* buf0 = reinterpret_cast<double*>(sm);
   double* buf1 = GS == 32 ? buf0 : buf0 + cap;
+  const int roff = (GS == 32 ? 1 : 2) * cap;  // OD: 1/max(tau_out, tau_w0) of slot i at i + roff
   const int TS = row_slot_bytes(h);
-  unsigned char* tab2 = sm + layer_bytes(h, GS == 32);  // [2][TS], 16-byte aligned
+  unsigned char* tab2 = sm + layer_bytes(h, GS == 32, OD);  // [2][TS], 16-byte aligned
   const int wid = gt >> 5, lane = gt & 31;
 
   const int s = item >> 5, f = (item >> 2) & 7, quad = item & 3;
@@ -199,15 +200,17 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
           const double w1 = wv0.x, w2 = wv0.y, w3 = wv1.x, w4 = wv1.y;
           const int b1 = min(a1, Hp), b2 = min(a1 - (a1 > 0), Hp);
           const int e1 = min(a2, Hp), e2 = min(a2 - (a2 > 0), Hp);
-          const double v1 = prev[b1 * Wp + e1];
-          const double v2 = prev[b2 * Wp + e1];
-          const double v3 = prev[b1 * Wp + e2];
-          const double v4 = prev[b2 * Wp + e2];
+          const int i1 = b1 * Wp + e1, i2 = b2 * Wp + e1, i3 = b1 * Wp + e2, i4 = b2 * Wp + e2;
+          const double v1 = prev[i1];
+          const double v2 = prev[i2];
+          const double v3 = prev[i3];
+          const double v4 = prev[i4];
           // w1*v1 as fma(w1, v1, -0.0): the same value for every input (the sum of the
           // exact product and -0 rounds like the product alone, and +0 + -0 = +0), on
           // GB300 issued as a DFMA, which retires at least as fast as a DMUL
           if (OD)
-            tin = od_interp(w1, w2, w3, w4, v1, v2, v3, v4, a.tau_w0, a.neg_zero);
+            tin = od_interp_r(w1, w2, w3, w4, v1, v2, v3, v4, prev[i1 + roff], prev[i2 + roff],
+                              prev[i3 + roff], prev[i4 + roff], a.neg_zero);
           else
             tin = fma(w4, v4, fma(w3, v3, fma(w2, v2, fma(w1, v1, a.neg_zero))));
         }
@@ -217,6 +220,7 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
           if (t0 - lane < 0) continue;
         }
         cur[a1 * W + a2] = tout;
+        if (OD) cur[a1 * W + a2 + roff] = od_recip(tout, a.tau_w0);
         opaque = opaque && bits_of(tout) >= a.exit_bits;
         const bool own = ((d == 2) || (d == 1 ? a2 < m : (a1 < m && a2 < m))) &&
                          (a1 > 0 || q1 > 0) && (a2 > 0 || q2 > 0);
@@ -396,8 +400,9 @@ __device__ __forceinline__ void trace_face_whole(const TraceArgs& a, const int i
 
   const int W = 2 * h + 1;
   double* ctr = reinterpret_cast<double*>(sm) + h * W + h;  // slot of (t1, t2): ctr[t1 W + t2]
+  const int roff = W * W;  // OD: 1/max(tau_out, tau_w0) of slot o at o + roff
   const int TS = row_slot_bytes(h);
-  unsigned char* tab2 = sm + face_buf_bytes(h);  // [2][TS], 16-byte aligned
+  unsigned char* tab2 = sm + face_buf_bytes(h, OD);  // [2][TS], 16-byte aligned
   const bool exit_ok = !COLDENS && a.early_exit;
   const double half_dts = 0.5 * dts;
   // interior tables of layer 1 (slot 1); layer m+1's (slot (m+1)&1) during layer m
@@ -459,8 +464,9 @@ __device__ __forceinline__ void trace_face_whole(const TraceArgs& a, const int i
         if constexpr (FIRST) {
           tin = half_dts * ds;
         } else if (OD) {
-          tin = od_interp(wv0.x, wv0.y, wv1.x, wv1.y, ctr[o1], ctr[o2], ctr[o3], ctr[o4], a.tau_w0,
-                          a.neg_zero);
+          tin = od_interp_r(wv0.x, wv0.y, wv1.x, wv1.y, ctr[o1], ctr[o2], ctr[o3], ctr[o4],
+                            ctr[o1 + roff], ctr[o2 + roff], ctr[o3 + roff], ctr[o4 + roff],
+                            a.neg_zero);
         } else if (__all_sync(0xffffffffu, cls != CLS_I)) {
           // rim row (w1 = w3 = 0), rim column (w1 = w2 = 0), axis t1 = 0 (w2 = w4 = 0),
           // axis t2 = 0 (w3 = w4 = 0)
@@ -481,6 +487,7 @@ __device__ __forceinline__ void trace_face_whole(const TraceArgs& a, const int i
         group_sync<GS>();  // every thread has read layer m-1 before any thread writes
         if (j >= total) continue;
         ctr[o1] = tout;
+        if (OD) ctr[o1 + roff] = od_recip(tout, a.tau_w0);
         opaque = opaque && bits_of(tout) >= a.exit_bits;
         const bool own = (d == 2) || (d == 1 ? a2 < m : (a1 < m && a2 < m));
         if (!own) continue;
@@ -536,7 +543,7 @@ __global__ void __launch_bounds__(BLOCK, 1152 / BLOCK) k_trace_faces(TraceArgs a
   if (a.skip && *a.skip) return;
   const int cap = (a.hcap + 1) * (a.hcap + 1);
   double* buf = reinterpret_cast<double*>(smem_raw);
-  for (int t = threadIdx.x; t < 2 * cap; t += BLOCK) buf[t] = 0.0;
+  for (int t = threadIdx.x; t < (OD ? 4 : 2) * cap; t += BLOCK) buf[t] = 0.0;
   unsigned nrate = 0;
   for (;;) {
     __syncthreads();
@@ -558,10 +565,10 @@ __global__ void __launch_bounds__(256, 4) k_trace_faces_warp(TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (a.skip && *a.skip) return;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* my = smem_raw + (size_t)wid * group_smem_bytes(a.hcap, true);
+  unsigned char* my = smem_raw + (size_t)wid * group_smem_bytes(a.hcap, true, OD);
   const int cap = (a.hcap + 1) * (a.hcap + 1);
   double* buf = reinterpret_cast<double*>(my);
-  for (int t = lane; t < cap; t += 32) buf[t] = 0.0;  // one layer buffer per warp
+  for (int t = lane; t < (OD ? 2 : 1) * cap; t += 32) buf[t] = 0.0;  // one layer buffer per warp
   __syncwarp();
   unsigned nrate = 0;
   for (;;) {
@@ -584,10 +591,10 @@ __global__ void __launch_bounds__(256, 3) k_trace_faces_whole_warp(TraceArgs a) 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (a.skip && *a.skip) return;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* my = smem_raw + (size_t)wid * whole_smem_bytes(a.hcap);
+  unsigned char* my = smem_raw + (size_t)wid * whole_smem_bytes(a.hcap, OD);
   const int W = 2 * a.hcap + 1;
   double* buf = reinterpret_cast<double*>(my);
-  for (int t = lane; t < W * W; t += 32) buf[t] = 0.0;  // one face buffer per warp
+  for (int t = lane; t < (OD ? 2 : 1) * W * W; t += 32) buf[t] = 0.0;  // one face buffer per warp
   __syncwarp();
   unsigned nrate = 0;
   for (;;) {
@@ -644,11 +651,11 @@ cudaError_t launch_trace_faces(Grid& g, const TraceArgs& a, int block, int grid,
   return e;
 }
 
-int faces_max_grid(int block, size_t smem, int wpb) {
+int faces_max_grid(int block, size_t smem, int wpb, bool od) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const void* fn = face_kernel(block, wpb, false, false);
+  const void* fn = face_kernel(block, wpb, false, od);
   if (!fn) return 0;
   const int threads = (block == 32 || block == 4) ? wpb * 32 : block;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
