@@ -26,24 +26,29 @@ __global__ void k_chemistry(int64_t n, const double* __restrict__ nH, double inv
     const double xs = x0[c];
     const double nh = nH[c] * inv_a3;
     const double xin = xavg_in[c];
-    double xa = xin, xnew = xs;
+    double xa = xin;
+    // x(t + dt) of the last pass only: its equilibrium value and y (rate <= 0: x0)
+    double xeq_last = xs, y_last = 0.0;
+    bool decays = false;
     for (int it = 0; it < maxit; ++it) {
       const double ne = nh * xa;
       const double rate = G + ne * (C_H + alpha_H);
       double xa_new;
-      if (rate > 0.0) {
+      decays = rate > 0.0;
+      if (decays) {
         const double xeq = (G + ne * C_H) / rate;
         const double y = dt * rate;
         xa_new = xeq + (xs - xeq) * (-expm1(-y) / y);
-        xnew = xeq + (xs - xeq) * exp(-y);
+        xeq_last = xeq;
+        y_last = y;
       } else {
         xa_new = xs;
-        xnew = xs;
       }
       const bool done = fabs(xa_new - xa) <= tol * xa_new;
       xa = xa_new;
       if (done) break;
     }
+    const double xnew = decays ? xeq_last + (xs - xeq_last) * exp(-y_last) : xs;
     xavg_out[c] = xa;
     xnew_out[c] = xnew;
     const double xhi_old = 1.0 - xin, xhi_new = 1.0 - xa;
