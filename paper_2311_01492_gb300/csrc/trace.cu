@@ -126,6 +126,7 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
   double* cur = buf1;
   int Hp = 0;
   const bool exit_ok = !COLDENS && a.early_exit;
+  int head_done = 0;  // warp mode: top cells of this layer traced in the previous layer's last round
   // precomputed row tables of this item's R^2 limit, if its window clips no layer:
   // blob of layer m at a.rtab + toff[m], toff[m+1] - toff[m] bytes
   const int* toff = nullptr;
@@ -148,6 +149,100 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
       }
     }
   }
+  // Warp mode, layers m >= 2 without the early exit: one cell of a layer (params
+  // L) per lane, all reads before the warp sync, the write after it.
+  struct LayerP {
+    int m, Hp, lc, lay, gbase;
+    const GeoRow* grow;
+    const int* rowpre;
+    const unsigned char* rowof;
+  };
+  auto warp_cell = [&](const LayerP& L, const int t, const bool act) {
+    const int a1 = L.rowof[t];
+    const int a2 = t - L.rowpre[a1];
+    const int x1 = wrapc(c1 + q1 * a1, N), x2 = wrapc(c2 + q2 * a2, N);
+    const int gidx = L.lay + x1 * m1 + x2;
+    const double dtp = __ldg(&fld[gidx]);
+    const GeoRow* gr = L.grow + a1 * (L.m + 1) + a2;
+    const double2 wv0 = __ldg(reinterpret_cast<const double2*>(gr));      // w1, w2
+    const double2 wv1 = __ldg(reinterpret_cast<const double2*>(gr) + 1);  // w3, w4
+    const double ds = __ldg(&gr->ds);
+    const int Wh = h + 1;
+    const int b1 = min(a1, L.Hp), b2 = min(a1 - (a1 > 0), L.Hp);
+    const int e1 = min(a2, L.Hp), e2 = min(a2 - (a2 > 0), L.Hp);
+    const int i1 = b1 * Wh + e1, i2 = b2 * Wh + e1, i3 = b1 * Wh + e2, i4 = b2 * Wh + e2;
+    double tin;
+    if (OD)
+      tin = od_interp_r(wv0.x, wv0.y, wv1.x, wv1.y, prev[i1], prev[i2], prev[i3], prev[i4],
+                        prev[i1 + roff], prev[i2 + roff], prev[i3 + roff], prev[i4 + roff],
+                        a.neg_zero);
+    else
+      tin = fma(wv1.y, prev[i4], fma(wv1.x, prev[i3], fma(wv0.y, prev[i2],
+                                                         fma(wv0.x, prev[i1], a.neg_zero))));
+    const double tout = fma(dtp, ds, tin);
+    __syncwarp();  // every lane has read its interpolants before any lane writes
+    if (!act) return;
+    cur[a1 * Wh + a2] = tout;
+    if (OD) cur[a1 * Wh + a2 + roff] = od_recip(tout, a.tau_w0);
+    const bool own = ((d == 2) || (d == 1 ? a2 < L.m : (a1 < L.m && a2 < L.m))) &&
+                     (a1 > 0 || q1 > 0) && (a2 > 0 || q2 > 0);
+    if (!own) return;
+    if (COLDENS || bits_of(tin) < a.tab.tau_max_bits) {
+      const int64_t cell = B.off + (d == 2 ? (x1 * N + x2) * N + L.lc : gidx);
+      if (COLDENS) {
+        a.coldens[cell] = tout / a.sigma0;
+      } else {
+        const GeoEntry* ge = &a.geo[L.gbase + ((max(a1, a2) * (max(a1, a2) + 1)) >> 1) + min(a1, a2)];
+        const double dcell = dtp * ds;
+        const double dG = cell_rate(a, nd * B.inv_cell3, nd * B.thin_fac, tin, tout, dcell, ge,
+                                    &a.invn[cell]);
+        ++nrate;
+        if (dG != 0.0) atomicAdd(&a.gamma[cell], dG);
+      }
+    }
+  };
+  // The cells of layer m not traced yet (all but its hd top ones), 32 per round in
+  // descending flat order.  A last round with k < 32 cells left gives its other
+  // lanes the top cells of layer m+1 when that is safe: those read layer m only in
+  // rows above the rows the k cells write (and write only rows above those the k
+  // cells read), and layer m+1's row table is in shared memory -- so they read
+  // exactly what they would read after layer m, and the partly filled rounds of
+  // the two layers become one.
+  auto warp_layer = [&](const int m, const int H, const int total, const int hd, const int lc,
+                        const int lay, const GeoRow* grow, const int gbase, const int* rowpre,
+                        const unsigned char* rowof, const int Hn) {
+    const LayerP Lc{m, Hp, lc, lay, gbase, grow, rowpre, rowof};
+    int t0 = total - 1 - hd;
+    for (; t0 >= 31; t0 -= 32) warp_cell(Lc, t0 - lane, true);
+    if (t0 < 0) return;
+    const int k = t0 + 1;  // cells left in layer m: flat indices 0..k-1
+    if (toff && m < Lmax && Hn <= h && m + 1 <= a.geo_mmax) {
+      cp_async_wait_all();  // layer m+1's row table (staged at the start of layer m)
+      __syncwarp();
+      const int nrn = min(Hn, lim1) + 1;
+      const int* pren = reinterpret_cast<const int*>(tab2 + ((m + 1) & 1) * TS);
+      const unsigned char* rown = reinterpret_cast<const unsigned char*>(pren + nrn + 1);
+      const int totn = pren[nrn];
+      const int head = min(32 - k, totn);
+      // rows: the k cells write (and read) rows <= rowof[k-1]; the head cells read
+      // rows >= min(rown[totn-head] - 1, H) and write rows >= rown[totn-head]
+      if (head > 0 && head < totn && min((int)rown[totn - head] - 1, H) > (int)rowof[k - 1]) {
+        const int lcn = wrapc(cd + sg * (m + 1), N);
+        const LayerP Ln{m + 1, H, lcn, lcn * md, (int)geo_index(m + 1, 0, 0),
+                        a.georow + georow_index(m + 1, 0, 0), pren, rown};
+        const bool mine = lane < k;
+        const LayerP L{mine ? Lc.m : Ln.m, mine ? Lc.Hp : Ln.Hp, mine ? Lc.lc : Ln.lc,
+                       mine ? Lc.lay : Ln.lay, mine ? Lc.gbase : Ln.gbase,
+                       mine ? Lc.grow : Ln.grow, mine ? Lc.rowpre : Ln.rowpre,
+                       mine ? Lc.rowof : Ln.rowof};
+        const int t = mine ? k - 1 - lane : totn - 1 - (lane - k);
+        warp_cell(L, max(t, 0), mine || lane - k < head);
+        head_done = head;
+        return;
+      }
+    }
+    warp_cell(Lc, max(t0 - lane, 0), t0 - lane >= 0);
+  };
   group_sync<GS>();
   for (int m = 1; m <= Lmax; ++m) {
     const int rem = R2 - m * m;
@@ -177,9 +272,17 @@ __device__ __forceinline__ void trace_face_item(const TraceArgs& a, const int it
     // predicated FP64 product in every round of every layer, and an FP64
     // instruction whose lanes are all predicated off still takes its full turn
     // on the FP64 pipe.
+    const int hd = head_done;
+    head_done = 0;
     auto cells = [&](auto first) {
       constexpr bool FIRST = decltype(first)::value;
-      for (int t0 = GS == 32 ? total - 1 : gt; GS == 32 ? t0 >= 0 : t0 < total;
+      if constexpr (GS == 32 && !FIRST) {
+        if (!exit_ok) {
+          warp_layer(m, H, total, hd, lc, lay, grow, gbase, rowpre, rowof, Hn);
+          return;
+        }
+      }
+      for (int t0 = GS == 32 ? total - 1 - hd : gt; GS == 32 ? t0 >= 0 : t0 < total;
            t0 += GS == 32 ? -32 : GS) {
         // warp mode: lanes take t0, t0-1, ..., t0-31; lanes below 0 recompute cell 0
         // and write nothing
