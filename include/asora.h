@@ -236,8 +236,9 @@ rt_status rt_set_schedule(rt_grid_t g, int block_big, int hsmall, int hface);
 
 /* Autotuner of RT_SCHED_BATCHED: times rt_raytrace on the registered fields and
  * sources for block_big in {128, 256} x hsmall in {0, 11, 15, 19, 22, 24, 27, 30}
- * (whole-face warps off), then hface in {9, 11, 13, 15, 17, 19} at the fastest pair; keeps
- * the fastest and returns it in *h_block, *h_hsmall, *h_hface (any may be NULL).
+ * (whole-face warps off), then hface in {9, 11, 13, 15, 17, 19} at the fastest pair, then
+ * hsmall again at that hface; keeps the fastest and returns it in *h_block, *h_hsmall,
+ * *h_hface (any may be NULL).
  * Finally times the plain (block-per-source) schedule once: RT_SCHED_AUTO takes
  * whichever of the two is faster.  With a cache file (may be NULL), a line
  * "<workload key> <block> <hsmall> <hface> <auto_plain>" whose key (box sizes,

@@ -1010,6 +1010,24 @@ rt_status rt_autotune(rt_grid_t h, const char* cache_path, int* h_block, int* h_
       bf = hf;
     }
   }
+  // stage 2b: the warp-mode threshold again, with the chosen whole-face threshold
+  // (whole faces take the small sources away from the warp mode, which shifts its
+  // best range)
+  if (bf > 0) {
+    g.hface = bf;
+    for (int hs : hss) {
+      if (st != RT_OK) break;
+      if (hs == 0 || hs == bh) continue;
+      g.hsmall = hs;
+      float t = 0.f;
+      if (!timed(t)) break;
+      if (t < best) {
+        best = t;
+        bh = hs;
+      }
+    }
+    g.hsmall = bh;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   dev_free(gam);
