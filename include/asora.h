@@ -231,7 +231,9 @@ typedef struct {
  * 256), the others by single warps (hsmall 0..32; 0 = CTAs only); of those,
  * sources whose largest layer half-width is at most hface (0..20; 0 = off) have
  * each face traced whole by one warp (every cell of a face once, no cell shared
- * between quadrants).  Defaults 128, 19, 13; results do not depend on the choice. */
+ * between quadrants).  rt_raytrace_backward uses block_big CTAs of 128 and
+ * min(hsmall, 27) (its warps hold more shared memory).  Defaults 128, 19, 13;
+ * results do not depend on the choice. */
 rt_status rt_set_schedule(rt_grid_t g, int block_big, int hsmall, int hface);
 
 /* Autotuner of RT_SCHED_BATCHED: times rt_raytrace on the registered fields and

@@ -803,16 +803,21 @@ rt_status rt_raytrace_backward(rt_grid_t h, const double* d_dL_dgamma, double* d
     g.dq_cap = g.nsrc;
   }
   TRY(cudaMemsetAsync(g.dq_merged, 0, g.nsrc * sizeof(double), g.stream));
-  // items of large sources by 128-thread CTAs, the rest one per warp (as the trace)
+  // items of large sources by 128-thread CTAs, the rest one per warp (as the trace,
+  // but with the warp-mode threshold capped at half-width 27: an adjoint warp keeps
+  // two layers and its layer records in shared memory, and beyond 27 too few of
+  // its warps stay resident -- 1e5 sources of the 250^3 workload took 1.5x longer
+  // at 30)
   const int hbig = face_hcap(g.max_r2, g.nmax);
   const int lcap = std::max(1, std::min(isqrt_h(g.max_r2), g.nmax / 2 + 1));
   const int n_items = 24 * g.nsrc;
+  const int hsmall_bwd = std::min(g.hsmall, 27);
   int split = n_items, hsm = 0, r2sm = 0;
-  if (g.hsmall > 0 && !g.r2_sorted_h.empty()) {
+  if (hsmall_bwd > 0 && !g.r2_sorted_h.empty()) {
     int lo = 0, hi = (int)g.r2_sorted_h.size();
     while (lo < hi) {
       const int mid = (lo + hi) / 2;
-      if (face_hcap(g.r2_sorted_h[mid], g.nmax) <= g.hsmall) hi = mid; else lo = mid + 1;
+      if (face_hcap(g.r2_sorted_h[mid], g.nmax) <= hsmall_bwd) hi = mid; else lo = mid + 1;
     }
     if (lo < (int)g.r2_sorted_h.size()) {
       split = 24 * lo;
